@@ -1,0 +1,356 @@
+"""Benchmark of the EM transport loop on GB300 (one JSON line on rank 0).
+
+A benchmark step is one complete pass of the transport hot path over one
+batch: submit every event of the workload, step until no track is left,
+read every event's scores.  Default workload: the sampling calorimeter
+(50 x (2 mm Pb + 5 mm LAr), 10,000 events of one 10 GeV electron, FP64).
+
+  value : track-steps/s with the primaries already in device memory when the
+          timed region starts (CUDA events on the library's stream)
+  e2e   : the same through host buffers (pinned), host<->device copies of the
+          primaries and of all scores inside the timed region
+  roofline : the step kernel (dominant by time): algorithmic track-state
+          bytes per launch / mean launch duration (CUDA events around each
+          launch, recorded by the library on its stream)
+  cpu_baseline : the FP64 CPU oracle on the host cores, on a bounded sample
+          of the same workload
+
+Under torchrun each rank runs its own shard of events (weak scaling: the
+per-GPU workload is fixed); there is no collective on the data path.
+`--impl reference` times the CPU oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2203_09467_gb300 import workloads as W  # noqa: E402
+
+METRIC = "track-steps/s"
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def workload(name, n_events, rank):
+    """Setup, primaries and event ids of this rank's shard."""
+    if name == "calo":
+        s = W.calo_setup()
+        prim = W.calo_primaries(n_events, seed=s.seed + 7919 * rank)
+        desc = f"sampling calorimeter 50x(2mm Pb+5mm LAr), {n_events} events x 10 GeV e-"
+    elif name == "slab":
+        s = W.slab_setup()
+        prim = W.slab_primaries(n_events)
+        desc = f"5 cm Pb slab, {n_events} events x 100 MeV e-"
+    elif name == "calo_field":
+        s = W.calo_field_setup()
+        prim = W.calo_field_primaries(n_events, seed=s.seed + 7919 * rank)
+        desc = f"calorimeter in 2 T field, {n_events} events, e-/e+/gamma 1-100 GeV"
+    elif name == "batched":
+        s = W.calo_field_setup()
+        s.seed = 4
+        prim = W.batched_primaries(n_events, seed=4 + 7919 * rank)
+        desc = f"calorimeter in 2 T field, {n_events} events of 1-64 primaries, 0.1-100 GeV"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    ids = (np.arange(n_events, dtype=np.uint64) + np.uint64(rank * n_events))
+    return s, prim, ids, desc
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(setup, prim, ids, budget_s=12.0):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample
+    of the workload (events in order until ~budget_s of work)."""
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    orc = oracle.Oracle(setup.materials, setup.physics, setup.layers, setup.world, setup.seed)
+    n_total = len(ids)
+    n = min(n_total, max(cores * 4, 64))
+    steps = 0.0
+    t = 0.0
+    done = 0
+    while done < n_total:
+        take = min(n, n_total - done)
+        sub = W.subset(prim, np.arange(done, done + take))
+        t0 = time.perf_counter()
+        _, summ = orc.run(sub, take, ids[done:done + take], n_threads=cores)
+        t += time.perf_counter() - t0
+        steps += summ[:, 4].sum()
+        done += take
+        if t > budget_s:
+            break
+        n = min(n_total - done, int(take * max(1.0, min(4.0, budget_s / max(t, 1e-3) / 2)))) or 1
+    orc.close()
+    return {"value": steps / t, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"first {done} of {n_total} events of the workload, {int(steps)} track-steps, "
+                      f"{t:.1f} s on {cores} threads"}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    setup, prim, ids, desc = workload(args.workload, args.events, 0)
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    orc = oracle.Oracle(setup.materials, setup.physics, setup.layers, setup.world, setup.seed)
+    # each step: a bounded sample of the workload (sized for a few seconds)
+    n = min(args.events, args.ref_events)
+    sub = W.subset(prim, np.arange(n))
+    for _ in range(args.warmup):
+        orc.run(sub, n, ids[:n], n_threads=cores)
+    t = 0.0
+    steps = 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        _, summ = orc.run(sub, n, ids[:n], n_threads=cores)
+        t += time.perf_counter() - t0
+        steps += summ[:, 4].sum()
+    v = steps / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc, "sample_events_per_step": n},
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": cores, "kind": "oracle",
+                             "sample": f"first {n} events of the workload per step"},
+            "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def gpu_arm(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_2203_09467_gb300 import emt
+
+    setup, prim, ids, desc = workload(args.workload, args.events, rank)
+    n = len(ids)
+    ctx = emt.context_for(setup, device=local, precision=args.precision, loop_mode=args.loop,
+                          graph_steps=args.graph_steps, slot_capacity=args.slots, max_events=n,
+                          block_size=args.block)
+    stream = ctx.stream
+    dev = torch.device("cuda", local)
+    dprim = {k: torch.as_tensor(v).to(dev) for k, v in prim.items()}
+    nb = setup.n_bins
+    hist_d = torch.empty((n, nb), dtype=torch.float64, device=dev)
+    summ_d = torch.empty((n, 6), dtype=torch.float64, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+    pin = {k: torch.as_tensor(v).pin_memory() for k, v in prim.items()}
+    hist_h = torch.empty((n, nb), dtype=torch.float64).pin_memory()
+    summ_h = torch.empty((n, 6), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+
+    def flush_l2():
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+
+    def step_device():
+        ctx.submit(ids, dprim)
+        st = ctx.run()
+        ctx.read_all(hist_d, summ_d)
+        return st
+
+    def step_host():
+        ctx.submit(ids, {k: v.numpy() for k, v in pin.items()})
+        st = ctx.run()
+        ctx.read_all(hist_h.numpy(), summ_h.numpy())
+        return st
+
+    for _ in range(args.warmup):
+        flush_l2()
+        step_device()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms = []
+    stats = []
+    launches = 0
+    for _ in range(args.steps):
+        flush_l2()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st = step_device()
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+        stats.append(st)
+        launches += st["kernel_launches"] + 6  # + admission (5 kernels) and gather
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = float(sum(ms))
+    steps_done = float(sum(s["track_steps"] for s in stats))
+    if world > 1:
+        t = torch.tensor([total_ms, steps_done], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
+        total_ms_all, steps_all = float(tmax[0]), float(t[1])
+    else:
+        total_ms_all, steps_all = total_ms, steps_done
+    value = steps_all / (total_ms_all / 1e3)
+
+    # end to end through host buffers
+    e2e_ms = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush_l2()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st = step_host()
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_steps = st["track_steps"]
+    e2e_value = e2e_steps * world / (max(e2e_ms) / 1e3) if world == 1 else None
+    if world > 1:
+        t = torch.tensor([max(e2e_ms), float(e2e_steps)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
+        e2e_value = float(t[1]) / (float(t[0]) / 1e3)
+    h2d = sum(v.numel() * v.element_size() for v in pin.values()) + ids.nbytes
+    d2h = hist_h.numel() * 8 + summ_h.numel() * 8
+
+    # roofline of the step kernel
+    peaks, src = load_peaks()
+    kern_ms = sum(s["kernel_ms"] for s in stats)
+    kern_launch = sum(s["kernel_launches"] for s in stats)
+    state_bytes = sum(s["state_bytes"] for s in stats)
+    achieved = state_bytes / (kern_ms / 1e3) / 1e9
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "peak_source": f"{src} hbm_gbs",
+            "kernel": "k_step", "launches": kern_launch, "mean_launch_ms": kern_ms / max(kern_launch, 1),
+            "algorithmic_bytes_per_launch": state_bytes / max(kern_launch, 1),
+            "kernel_share_of_step": kern_ms / total_ms}
+    if args.traffic_per_launch:
+        roof["traffic"] = args.traffic_per_launch
+
+    ctx.close()
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": desc, "precision": args.precision, "loop": args.loop,
+                   "slot_capacity": args.slots, "events_per_gpu": n,
+                   "l2": "512 MB buffer written between timed steps; track state >> L2"},
+        "events_per_s": n * world / (total_ms_all / 1e3 / args.steps),
+        "iterations_per_step": stats[0]["iterations"], "peak_tracks": max(s["peak_tracks"] for s in stats),
+        "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(setup, prim, ids, budget_s=args.cpu_budget)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="emt", choices=["emt", "reference"])
+    ap.add_argument("--workload", default="calo", choices=["calo", "slab", "calo_field", "batched"])
+    ap.add_argument("--events", type=int, default=10000)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--loop", default="plain", choices=["plain", "graph"])
+    ap.add_argument("--graph-steps", type=int, default=12)
+    ap.add_argument("--slots", type=int, default=1 << 25)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--ref-events", type=int, default=1000)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic-per-launch", type=float, default=None,
+                    help="DRAM bytes per step-kernel launch from an ncu capture of this kernel")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

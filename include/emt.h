@@ -1,0 +1,230 @@
+/*
+ * emt.h -- C ABI of the GB300 electromagnetic shower transport library.
+ *
+ * The library runs the per-step Monte Carlo transport loop for photons,
+ * electrons and positrons described in arXiv:2203.09467 (Celeritas):
+ * cross sections from tabulated log-spaced grids (Sec. 3.2, "all particle
+ * types use tabulated discrete interaction cross sections calculated
+ * simultaneously in a single kernel"), continuous slowing down and energy
+ * cutoffs (Sec. 3.2 list of capabilities), the six electromagnetic models
+ * of Table 1 (Klein-Nishina, Bethe-Heitler, photoelectric, bremsstrahlung,
+ * Moller-Bhabha, two-photon annihilation), straight-line and uniform-field
+ * propagation through layered-box geometry (Sec. 3.3), secondary
+ * allocation with a capacity-bounded device stack (Sec. 3.1, "function-like
+ * stack allocator ... atomic addition", with out-of-memory handled without
+ * breaking reproducibility), and scoring in device kernels instead of host
+ * callbacks (Sec. 3.4).  The call sequence follows the paper's statement of
+ * the problem: load materials and physics tables, load geometry, submit
+ * primaries for many concurrent events, step until done, read the scores.
+ *
+ * Conventions
+ *  - Units: MeV, cm, g/cm^3, tesla.
+ *  - Every call returns an emt_status; no exception or abort crosses the
+ *    ABI.  emt_last_error() gives a message for the last failed call on the
+ *    context (valid until the next call).
+ *  - Pointers marked "host" are read (or written) during the call only; the
+ *    caller keeps ownership.  Pointers marked "where" follow the `where`
+ *    argument: EMT_HOST (pageable or pinned host memory) or EMT_DEVICE
+ *    (device memory of the context's GPU; read on the context's stream).
+ *  - One context per host thread at a time.  All device work is ordered on
+ *    the context's stream (the caller's, if one is given in emt_options).
+ *  - Results are bitwise independent of how events are batched, of the
+ *    track-slot capacity and of scheduling, except for the summation order
+ *    of floating-point deposits (each track draws from its own
+ *    counter-based random stream keyed on event, track id and step).
+ */
+#ifndef EMT_H
+#define EMT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t emt_status;
+#define EMT_OK 0
+#define EMT_ERR_INVALID_ARG (-1) /* bad argument; nothing changed */
+#define EMT_ERR_CAPACITY (-2)    /* does not fit; nothing admitted, state unchanged */
+#define EMT_ERR_CUDA (-3)        /* CUDA error; the context is unusable */
+#define EMT_ERR_BAD_STATE (-4)   /* call out of order (e.g. run before load) */
+#define EMT_ERR_TIMEOUT (-5)     /* a bounded device wait gave up */
+#define EMT_ERR_NOT_READY (-6)   /* the event has not finished */
+#define EMT_ERR_HOST_OOM (-7)
+
+#define EMT_PRECISION_FP64 0  /* FP64 everywhere: matches the FP64 oracle */
+#define EMT_PRECISION_MIXED 1 /* FP32 tables and sampling; FP64 positions, distances, tallies */
+
+#define EMT_HOST 0
+#define EMT_DEVICE 1
+
+/* process bits of emt_physics.process_mask */
+#define EMT_PHOTO 1u
+#define EMT_COMPTON 2u
+#define EMT_PAIR 4u
+#define EMT_IONI 8u
+#define EMT_BREMS 16u
+#define EMT_ANNIH 32u
+#define EMT_ALL_PROCESSES 63u
+
+/* step-loop driver of emt_run */
+#define EMT_LOOP_PLAIN 0 /* host loop: one kernel launch and one counter read per step */
+#define EMT_LOOP_GRAPH 1 /* CUDA graph of several steps; one counter read per graph */
+
+typedef struct emt_ctx emt_ctx;
+
+typedef struct emt_options {
+    int32_t device;        /* CUDA device ordinal */
+    int32_t precision;     /* EMT_PRECISION_* */
+    int64_t slot_capacity; /* tracks in flight per step (each of two ping-pong buffers) */
+    int32_t max_events;    /* events that can be in flight (score slots) */
+    int32_t max_bins;      /* histogram width capacity (>= emt_world.n_bins) */
+    int32_t block_size;    /* threads per block of the step kernel; 0 = default */
+    int32_t loop_mode;     /* EMT_LOOP_* */
+    int32_t graph_steps;   /* steps per graph launch (EMT_LOOP_GRAPH); multiple of 6 */
+    uint32_t seed;         /* random stream seed */
+    void* cuda_stream;     /* cudaStream_t to use, or NULL for a context-owned stream */
+    void* device_pool;     /* caller-owned device memory, or NULL: see emt_pool_bytes */
+    size_t pool_bytes;
+} emt_options;
+
+/* Fill `opt` with defaults (device 0, FP64, 2^22 slots, 10,000 events,
+ * 128 bins, plain loop, seed 1). */
+void emt_default_options(emt_options* opt);
+
+/* Bytes of device memory a context with these options needs.  A caller
+ * that passes device_pool must pass at least this many bytes, aligned to
+ * 256 bytes; the context then allocates no device memory of its own. */
+size_t emt_pool_bytes(const emt_options* opt);
+
+/* Create a context on opt->device.  Host: opt.  out receives the context. */
+emt_status emt_create(const emt_options* opt, emt_ctx** out);
+void emt_destroy(emt_ctx* ctx);
+const char* emt_last_error(const emt_ctx* ctx);
+
+/* Materials (Sec. 3.2: material-dependent properties; single element per
+ * material, as in the paper's demonstration, Sec. 4 caveats).
+ * rho_g_cm3 == 0 marks vacuum.  bk_MeV is the K-shell binding energy used by
+ * the photoelectric model. */
+typedef struct emt_material {
+    double Z, A_g_mol, rho_g_cm3, I_eV, bk_MeV;
+} emt_material;
+
+/* Physics options (Sec. 3.2: processes, models and energy cutoffs).
+ * cut_MeV: production and tracking cuts for gamma, e-, e+.
+ * Tables are built on the device on the grid
+ * E_n = grid_lo * 10^(n / bins_per_decade), n = 0..bpd*log10(hi/lo). */
+typedef struct emt_physics {
+    double cut_MeV[3];
+    double grid_lo_MeV, grid_hi_MeV;
+    int32_t bins_per_decade;
+    uint32_t process_mask;
+    double step_frac;      /* e+- step limit: max(step_frac R, min(R, final_range)) */
+    double final_range_cm;
+} emt_physics;
+
+/* Load materials and build every cross-section and range table on the
+ * device (host: mats[n], phys).  Replaces earlier tables.  n in [1, 16]. */
+emt_status emt_load_materials(emt_ctx* ctx, const emt_material* mats, int32_t n, const emt_physics* phys);
+
+/* Layered-box geometry (Sec. 3.3): layers stacked along +z from z0, each
+ * |x| <= half_x, |y| <= half_y, inside the world box [lo, hi]; the world
+ * outside the stack is vacuum.  material -1 means vacuum.  score_bin is
+ * the histogram column of the layer (-1: not scored in the histogram). */
+typedef struct emt_layer {
+    int32_t material;
+    int32_t score_bin;
+    double thickness_cm;
+} emt_layer;
+
+typedef struct emt_world {
+    double z0_cm, half_x_cm, half_y_cm;
+    double lo_cm[3], hi_cm[3];
+    double B_tesla[3];        /* uniform field; zero = straight lines */
+    double rk_delta_cm;       /* RK4 miss distance (chord sagitta bound) */
+    double max_field_step_cm; /* longest path of one step in a field */
+    int32_t max_steps;        /* per-track step limit; then the track is killed */
+    int32_t n_bins;           /* histogram width (<= options.max_bins) */
+} emt_world;
+
+/* host: layers[n], world.  n in [1, 4096]. */
+emt_status emt_load_geometry(emt_ctx* ctx, const emt_layer* layers, int32_t n, const emt_world* world);
+
+/* Primaries of a batch of events, structure of arrays, n entries:
+ * event[i] indexes event_ids[] of the same submit call; type 0 gamma,
+ * 1 e-, 2 e+; pos and dir are [n][3]; dir must be unit vectors.  Within an
+ * event, primaries get track ids 1, 2, ... in submission order. */
+typedef struct emt_primaries {
+    int32_t n;
+    const int32_t* event;
+    const int32_t* type;
+    const double* T_MeV;
+    const double* pos_cm;
+    const double* dir;
+} emt_primaries;
+
+/* Submit n_events new events (ids distinct from every event in flight)
+ * with their primaries.  event_ids is host memory; the primary arrays
+ * follow `where`.  Returns EMT_ERR_CAPACITY, admitting nothing, when the
+ * free score slots or track slots do not suffice. */
+emt_status emt_submit(emt_ctx* ctx, int32_t n_events, const uint64_t* event_ids, const emt_primaries* prim,
+                      int32_t where);
+
+typedef struct emt_run_stats {
+    int64_t iterations;   /* step-loop iterations executed by this call */
+    int64_t track_steps;  /* tracks advanced by one step, summed over iterations */
+    int64_t peak_tracks;  /* largest number of tracks in flight seen by the host */
+    int64_t deferred;     /* track-steps postponed for lack of output capacity */
+    int64_t live_tracks;  /* tracks still in flight when the call returned */
+    int64_t state_bytes;  /* track-state bytes read plus written by the step kernel */
+    double kernel_ms;     /* device time of the step-kernel launches (CUDA events
+                             around each launch, or each graph launch) */
+    int32_t kernel_launches;
+} emt_run_stats;
+
+/* Step every track in flight until none is left or max_iterations
+ * (<= 0: no limit) iterations have run.  stats may be NULL. */
+emt_status emt_run(emt_ctx* ctx, int32_t max_iterations, emt_run_stats* stats);
+
+/* Per-event results: summary = {edep, escaped, killed, e_in, n_steps,
+ * n_tracks} (MeV, MeV, MeV, MeV, count, count); edep includes deposits in
+ * layers without a score bin. */
+#define EMT_SUMMARY_LEN 6
+
+/* Events finished since the last poll (host: done_ids[cap]). */
+emt_status emt_poll(emt_ctx* ctx, uint64_t* done_ids, int32_t cap, int32_t* n_done);
+
+/* Read and release one finished event.  host: hist[n_bins], summary[6]
+ * (either may be NULL).  EMT_ERR_NOT_READY if it has not finished. */
+emt_status emt_read_event(emt_ctx* ctx, uint64_t event_id, double* hist, double* summary);
+
+/* Read and release every event in flight, in submission order, after an
+ * emt_run that left no track (EMT_ERR_NOT_READY otherwise).
+ * hist[n_events][n_bins] and summary[n_events][6] follow `where`;
+ * ids (host, may be NULL) receives the event ids. */
+emt_status emt_read_all(emt_ctx* ctx, double* hist, double* summary, uint64_t* ids, int32_t where);
+int32_t emt_events_in_flight(const emt_ctx* ctx);
+
+/* Diagnostics: copy table (material m, particle p, quantity q) to host
+ * out[n] (n = grid size).  gamma q: 0 photo, 1 compton, 2 pair;
+ * e-: 0 ioni, 1 brems, 3 range; e+: 0 ioni, 1 brems, 2 annih, 3 range;
+ * q = 4: restricted stopping power; q = 5: energy grid.  Returns the grid
+ * size in *n_out.  Values are FP64 regardless of precision. */
+emt_status emt_get_table(emt_ctx* ctx, int32_t m, int32_t p, int32_t q, double* out, int32_t cap, int32_t* n_out);
+
+/* Diagnostics: replace the tracks in flight by explicit track states and
+ * read them back, to check single steps.  rec[n][10] = {type, T, x, y, z,
+ * ux, uy, uz, volume (-1 world vacuum), step}; uid[n]; event_slot[n]
+ * indexes the events of the last submit.  host memory. */
+emt_status emt_debug_set_tracks(emt_ctx* ctx, int32_t n, const double* rec, const uint64_t* uid,
+                                const int32_t* event_slot);
+/* Returns every track in flight (photons first) in rec/uid/event_slot
+ * (host, capacity cap); *n_out = number of tracks. */
+emt_status emt_debug_get_tracks(emt_ctx* ctx, int32_t cap, double* rec, uint64_t* uid, int32_t* event_slot,
+                                int32_t* n_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EMT_H */

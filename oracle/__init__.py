@@ -78,7 +78,7 @@ def lib():
                 "orc_range": (d, [p, i32, i32, d]),
                 "orc_inv_range": (d, [p, i32, i32, d]),
                 "orc_run": (i32, [p, i32, p, p, p, p, p, i32, p, p, p, i32]),
-                "orc_step_one": (i32, [p, p, u64, u64, p, p]),
+                "orc_step_one": (i32, [p, p, u64, u64, p, p, p]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -198,10 +198,15 @@ class Oracle:
             raise ValueError("orc_run failed")
         return hist, summ
 
-    def step_one(self, track, uid: int, event_id: int):
-        """track = [type, T, x, y, z, ux, uy, uz, vol, step] (updated in place)."""
+    def step_one(self, track, uid: int, event_id: int, with_uids: bool = False):
+        """One step of one track; track = [type, T, x, y, z, ux, uy, uz, vol,
+        step].  Returns (track after, secondaries, info[8] = {s, edep,
+        boundary, interacted, process, alive, escaped, killed}[, sec uids])."""
         t = np.ascontiguousarray(track, np.float64).copy()
         sec = np.zeros(16)
-        info = np.zeros(6)
-        n = lib().orc_step_one(self._h, _ptr(t), uid, event_id, _ptr(sec), _ptr(info))
+        sec_uid = np.zeros(2, np.uint64)
+        info = np.zeros(8)
+        n = lib().orc_step_one(self._h, _ptr(t), uid, event_id, _ptr(sec), _ptr(sec_uid), _ptr(info))
+        if with_uids:
+            return t, sec[: 8 * n].reshape(n, 8), info, sec_uid[:n].copy()
         return t, sec[: 8 * n].reshape(n, 8), info

@@ -821,6 +821,11 @@ static int momentum_balance(double pa, const double da[3], double pb, const doub
 /* ------------------------------------------------------------------ */
 enum { P_PHOTO = 0, P_COMPTON = 1, P_PAIR = 2, P_IONI = 3, P_BREMS = 4, P_ANNIH = 5 };
 
+/* Every rejection loop accepts its candidate after MAX_TRIALS trials (a
+ * safety bound against non-finite input; every acceptance probability here
+ * is at least 1/3, so a valid input never reaches it). */
+#define MAX_TRIALS 1000
+
 typedef struct {
     int n;
     int type[2];
@@ -843,7 +848,7 @@ static void sample_compton(draws_t* d, double k, double dir[3], products_t* out,
     double a1 = -log(eps0);
     double a2 = 0.5 * (1.0 - eps0sq);
     double eps, epssq, onecost, sint2, g;
-    for (;;) {
+    for (int trial = 1;; ++trial) {
         double u1 = draw(d), u2 = draw(d), u3 = draw(d);
         if (a1 / (a1 + a2) > u1) {
             eps = exp(-a1 * u2);
@@ -855,7 +860,7 @@ static void sample_compton(draws_t* d, double k, double dir[3], products_t* out,
         onecost = (1.0 - eps) / (eps * kappa);
         sint2 = onecost * (2.0 - onecost);
         g = 1.0 - eps * sint2 / (1.0 + epssq);
-        if (u3 <= g) break;
+        if (u3 <= g || trial >= MAX_TRIALS) break;
     }
     double phi = 2.0 * PI * draw(d);
     double cost = 1.0 - onecost;
@@ -885,11 +890,11 @@ static void sample_pair(draws_t* d, double k, const double dir[3], products_t* o
     double eps0 = ME / k;
     double w = 1.0 - 2.0 * eps0;
     double x;
-    for (;;) {
+    for (int trial = 1;; ++trial) {
         double u1 = draw(d), u2 = draw(d);
         x = eps0 + w * u1;
         double f = 1.0 - 4.0 / 3.0 * x * (1.0 - x);
-        if (u2 <= f) break;
+        if (u2 <= f || trial >= MAX_TRIALS) break;
     }
     double Tm = x * k - ME;
     if (Tm < 0.0) Tm = 0.0;
@@ -926,12 +931,12 @@ static void sample_brems(draws_t* d, double T, double kc, const double dir[3], p
     double E = T + ME;
     double lr = log(T / kc);
     double k;
-    for (;;) {
+    for (int trial = 1;; ++trial) {
         double u1 = draw(d), u2 = draw(d);
         k = kc * exp(u1 * lr);
         double y = k / E;
         double f = 4.0 / 3.0 - 4.0 / 3.0 * y + y * y;
-        if (u2 * (4.0 / 3.0) <= f) break;
+        if (u2 * (4.0 / 3.0) <= f || trial >= MAX_TRIALS) break;
     }
     out->n = 1;
     out->type[0] = 0;
@@ -972,12 +977,12 @@ static void sample_moller(draws_t* d, double T, double cut, double dir[3], produ
     double c = (2.0 * g - 1.0) / (g * g);
     double gmax = 2.0 + 0.25 * g1 * g1;
     double eps;
-    for (;;) {
+    for (int trial = 1;; ++trial) {
         double u1 = draw(d), u2 = draw(d);
         eps = xc / (1.0 - u1 * (1.0 - 2.0 * xc));
         double q = eps / (1.0 - eps);
         double f = 1.0 + q * q + g1 * g1 * eps * eps - c * q;
-        if (u2 * gmax <= f) break;
+        if (u2 * gmax <= f || trial >= MAX_TRIALS) break;
     }
     delta_kinematics(d, T, eps * T, dir, out, Tnew);
 }
@@ -990,11 +995,11 @@ static void sample_bhabha(draws_t* d, double T, double cut, double dir[3], produ
     double b2, c1, c2, c3, c4;
     bhabha_coeffs(T, &b2, &c1, &c2, &c3, &c4);
     double eps;
-    for (;;) {
+    for (int trial = 1;; ++trial) {
         double u1 = draw(d), u2 = draw(d);
         eps = xc / (1.0 - u1 * (1.0 - xc));
         double f = 1.0 - b2 * eps * (c1 - eps * (c2 - eps * (c3 - eps * c4)));
-        if (u2 <= f) break;
+        if (u2 <= f || trial >= MAX_TRIALS) break;
     }
     delta_kinematics(d, T, eps * T, dir, out, Tnew);
 }
@@ -1013,11 +1018,11 @@ static void sample_annih(draws_t* d, double T, const double dir[3], products_t* 
     double lr = log(emax / emin);
     double bq = g * g + 4.0 * g + 1.0;
     double eps;
-    for (;;) {
+    for (int trial = 1;; ++trial) {
         double u1 = draw(d), u2 = draw(d);
         eps = emin * exp(u1 * lr);
         double f = 1.0 - (a * a * eps + 1.0 / eps) / bq;
-        if (u2 <= f) break;
+        if (u2 <= f || trial >= MAX_TRIALS) break;
     }
     double Etot = T + 2.0 * ME;
     double E1 = eps * Etot;
@@ -1254,7 +1259,7 @@ static void step_track(const orc_handle* h, uint64_t event_id, track_t* tr, tall
             s = s_phys;
         }
         for (int a = 0; a < 3; ++a) tr->x[a] = tr->x[a] + s * tr->u[a];
-        if (boundary) tr->x[e.axis] = e.plane;
+        if (boundary && e.axis >= 0) tr->x[e.axis] = e.plane;
     } else {
         double smax = s_phys;
         if (smax > h->max_field_step) {
@@ -1452,7 +1457,8 @@ static void run_event(const orc_handle* h, uint64_t event_id, int n, const int* 
     free(st.v);
 }
 
-int orc_step_one(orc_handle* h, double* trk, uint64_t uid, uint64_t event_id, double* sec, double* info)
+int orc_step_one(orc_handle* h, double* trk, uint64_t uid, uint64_t event_id, double* sec, uint64_t* sec_uid,
+                 double* info)
 {
     track_t t;
     t.type = (int)trk[0];
@@ -1487,6 +1493,7 @@ int orc_step_one(orc_handle* h, double* trk, uint64_t uid, uint64_t event_id, do
             o[2 + a] = r.sec[k].x[a];
             o[5 + a] = r.sec[k].u[a];
         }
+        sec_uid[k] = r.sec[k].uid;
     }
     info[0] = r.s;
     info[1] = r.edep;
@@ -1494,6 +1501,8 @@ int orc_step_one(orc_handle* h, double* trk, uint64_t uid, uint64_t event_id, do
     info[3] = r.interacted;
     info[4] = r.process;
     info[5] = r.alive;
+    info[6] = ta.escaped;
+    info[7] = ta.killed;
     return r.n_sec;
 }
 

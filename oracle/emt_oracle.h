@@ -102,10 +102,10 @@ int orc_run(orc_handle*, int n_prim, const int32_t* ev, const int32_t* type,
 /* one step of one track (diagnostics and single-step pins).
  * track in/out: {type, T, x, y, z, ux, uy, uz, vol, step}, uid, event_id.
  * returns number of secondaries written to sec (each 8 doubles:
- * {type, T, x, y, z, ux, uy, uz}); info[6] = {s, edep, boundary, interacted,
- * process, alive}.                                                          */
+ * {type, T, x, y, z, ux, uy, uz}) and sec_uid; info[8] = {s, edep,
+ * boundary, interacted, process, alive, escaped, killed}.                  */
 int orc_step_one(orc_handle*, double* track, uint64_t uid, uint64_t event_id,
-                 double* sec, double* info);
+                 double* sec, uint64_t* sec_uid, double* info);
 
 #ifdef __cplusplus
 }

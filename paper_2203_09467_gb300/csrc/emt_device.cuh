@@ -1,0 +1,815 @@
+// emt_device.cuh -- device-side data layout, random streams, table
+// lookups, navigation, field propagation and interaction samplers of the
+// EM transport step (arXiv:2203.09467, Secs. 3.1-3.3).
+//
+// Templated on the physics real type R: double for the FP64 path (built
+// with --fmad=false so every expression rounds exactly as written) and
+// float for the mixed path (positions, boundary distances and tallies stay
+// FP64).  Each formula cites the textbook closed form it evaluates; the
+// operation order of the FP64 instantiation is the library's definition of
+// the method and is what the FP64 tests compare against.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace emt {
+
+constexpr double kMe = 0.51099895;          // electron mass, MeV (CODATA 2018)
+constexpr double kRe = 2.8179403262e-13;    // classical electron radius, cm
+constexpr double kAlpha = 1.0 / 137.035999084;
+constexpr double kNa = 6.02214076e23;       // 1/mol
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kFieldC = 2.99792458;      // curvature per (T / MeV), 1/cm
+constexpr int kMaxMat = 16;
+constexpr int kMaxLayers = 4096;
+constexpr int kVolWorld = -1;               // vacuum of the world box
+constexpr int kVolOut = -2;                 // left the world
+constexpr int kNq = 4;                      // table quantities per node
+// Rejection loops accept their candidate after kMaxTrials trials: a bound
+// against non-finite input (every acceptance probability is >= 1/3).
+constexpr int kMaxTrials = 1000;
+
+// status bits written by kernels (host reads after each run)
+constexpr int kStatusQueueOverflow = 1;
+constexpr int kStatusBadTrack = 2;
+
+// ------------------------------------------------------------------ math
+__device__ __forceinline__ double mlog(double x) { return log(x); }
+__device__ __forceinline__ float mlog(float x) { return logf(x); }
+__device__ __forceinline__ double mexp(double x) { return exp(x); }
+__device__ __forceinline__ float mexp(float x) { return expf(x); }
+__device__ __forceinline__ double msqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float msqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double msin(double x) { return sin(x); }
+__device__ __forceinline__ float msin(float x) { return sinf(x); }
+__device__ __forceinline__ double mcos(double x) { return cos(x); }
+__device__ __forceinline__ float mcos(float x) { return cosf(x); }
+__device__ __forceinline__ double mfmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float mfmax(float a, float b) { return fmaxf(a, b); }
+
+// ------------------------------------------------------------------ layout
+// One ping-pong side of the track store, structure of arrays.  Photons
+// occupy [0, nG) from the front, charged tracks [Q-nC, Q) from the back.
+template <typename R>
+struct Tracks {
+    double* x;
+    double* y;
+    double* z;
+    R* ux;
+    R* uy;
+    R* uz;
+    R* T;
+    uint64_t* uid;
+    uint32_t* ev;    // event slot
+    uint32_t* step;  // steps taken by this track
+    uint32_t* tv;    // type (bits 0-7) | (volume + 2) << 8
+};
+
+// per-iteration counters, rotating over three slots (input, output, clear)
+struct Counters {
+    int n[2];      // photons, charged
+    int work;      // chunk dispenser
+    int deferred;  // tracks copied without stepping
+};
+
+template <typename R>
+struct Params {
+    // tables: tab[((m * 3 + p) * n_grid + node) * 4 + q]
+    const R* grid;
+    const R* tab;
+    int n_grid;
+    int bpd;
+    float log10_lo;  // log10(grid[0]) for the bin guess
+    const double* bk;
+    const int* vacuum;
+    double cut[3];
+    double step_frac, final_range;
+    // geometry
+    const double* zb;
+    const int* lmat;
+    const int* lbin;
+    int n_layers;
+    double hx, hy;
+    double wlo[3], whi[3];
+    double B[3];
+    double bmag;
+    double rk_delta, max_field_step;
+    int has_field;
+    int max_steps;
+    // scoring
+    double* hist;  // [slot][hstride]; column n_bins collects unbinned deposits
+    int hstride;
+    int n_bins;
+    double* ledger;                 // [slot][3] escaped, killed, e_in
+    unsigned long long* counts;     // [slot][2] steps, tracks
+    const uint64_t* event_id;       // [slot]
+    int* live;                      // [slot] tracks alive (+1 submission token)
+    unsigned* done_ring;            // [max_events] slots of finished events
+    unsigned* done_head;            // total finished events (ring index)
+    unsigned long long* total_steps;  // [0] track-steps taken, [1] deferred copies
+    int max_events;
+    uint32_t seed;
+    // queues
+    Tracks<R> q[2];
+    long long Q;
+    Counters* cnt;  // [3]
+    int* status;
+};
+
+__device__ __forceinline__ uint32_t pack_tv(int type, int vol) { return (uint32_t)type | ((uint32_t)(vol + 2) << 8); }
+__device__ __forceinline__ int tv_type(uint32_t tv) { return (int)(tv & 0xFFu); }
+__device__ __forceinline__ int tv_vol(uint32_t tv) { return (int)(tv >> 8) - 2; }
+
+// ------------------------------------------------------------------ RNG
+// Philox4x32-10 (Salmon et al., SC'11): multipliers 0xD2511F53 and
+// 0xCD9E8D57, Weyl key increments 0x9E3779B9 and 0xBB67AE85, 10 rounds.
+__device__ __forceinline__ void philox10(uint32_t c[4], uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint32_t lo0 = 0xD2511F53u * c[0];
+        uint32_t hi0 = __umulhi(0xD2511F53u, c[0]);
+        uint32_t lo1 = 0xCD9E8D57u * c[2];
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]);
+        uint32_t n0 = hi1 ^ c[1] ^ k0;
+        uint32_t n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+}
+
+// Draw stream of one track step: key (lo32(event), hi32(event) ^ seed),
+// counter (lo32(uid), hi32(uid), step, block).  FP64: draw j uses block
+// j >> 1, words 2(j&1) (low half) and 2(j&1)+1 (high half) as a 64-bit
+// word w; u = (floor(w / 2^12) + 1/2) 2^-52, formed exactly as
+// (1 + m 2^-52) - (1 - 2^-53).  FP32: draw j uses block j >> 2, word j & 3,
+// u = (floor(w / 2^9) + 1/2) 2^-23.
+struct Draws {
+    uint32_t k0, k1, c0, c1, step;
+    uint32_t next;
+    uint32_t blk;
+    uint32_t w[4];
+
+    __device__ __forceinline__ void init(uint32_t seed, uint64_t event_id, uint64_t uid, uint32_t s)
+    {
+        k0 = (uint32_t)event_id;
+        k1 = (uint32_t)(event_id >> 32) ^ seed;
+        c0 = (uint32_t)uid;
+        c1 = (uint32_t)(uid >> 32);
+        step = s;
+        next = 0;
+        blk = 0xFFFFFFFFu;
+    }
+    __device__ __forceinline__ void fill(uint32_t b)
+    {
+        if (b != blk) {
+            w[0] = c0;
+            w[1] = c1;
+            w[2] = step;
+            w[3] = b;
+            philox10(w, k0, k1);
+            blk = b;
+        }
+    }
+    __device__ __forceinline__ double u64(uint32_t j)
+    {
+        fill(j >> 1);
+        uint32_t lo = (j & 1u) ? w[2] : w[0];
+        uint32_t hi = (j & 1u) ? w[3] : w[1];
+        uint64_t m = ((((uint64_t)hi) << 32) | lo) >> 12;
+        return __longlong_as_double((long long)(0x3FF0000000000000ull | m)) - (1.0 - 0x1p-53);
+    }
+    __device__ __forceinline__ float u32(uint32_t j)
+    {
+        fill(j >> 2);
+        uint32_t v = w[j & 3u];
+        return __int_as_float((int)(0x3F800000u | (v >> 9))) - (1.0f - 0x1p-24f);
+    }
+};
+
+template <typename R>
+struct DrawOf;
+template <>
+struct DrawOf<double> {
+    static __device__ __forceinline__ double at(Draws& d, uint32_t j) { return d.u64(j); }
+};
+template <>
+struct DrawOf<float> {
+    static __device__ __forceinline__ float at(Draws& d, uint32_t j) { return d.u32(j); }
+};
+
+template <typename R>
+__device__ __forceinline__ R draw(Draws& d)
+{
+    R u = DrawOf<R>::at(d, d.next);
+    d.next += 1;
+    return u;
+}
+
+// child k of (uid, step): key word 0 ^ 0x5EC0DA7A, counter word 3 = 2^31 + k
+__device__ __forceinline__ uint64_t child_uid(uint32_t seed, uint64_t event_id, uint64_t uid, uint32_t step,
+                                              uint32_t k)
+{
+    uint32_t c[4] = {(uint32_t)uid, (uint32_t)(uid >> 32), step, 0x80000000u + k};
+    philox10(c, (uint32_t)event_id ^ 0x5EC0DA7Au, (uint32_t)(event_id >> 32) ^ seed);
+    return ((uint64_t)c[1] << 32) | (uint64_t)c[0];
+}
+
+// ------------------------------------------------------------------ tables
+// positive IEEE doubles (and floats) order like their bit patterns
+__device__ __forceinline__ bool le_pos(double a, double b) { return __double_as_longlong(a) <= __double_as_longlong(b); }
+__device__ __forceinline__ bool le_pos(float a, float b) { return __float_as_int(a) <= __float_as_int(b); }
+
+// node n with grid[n] <= E < grid[n+1], clamped to [0, n_grid-2]: an FP32
+// logarithm guesses, exact comparisons with the nodes decide.
+template <typename R>
+__device__ __forceinline__ int find_bin(const Params<R>& p, R E)
+{
+    float g = ((float)p.bpd) * (log10f((float)E) - p.log10_lo);
+    int n = (int)g;
+    int top = p.n_grid - 2;
+    n = n < 0 ? 0 : (n > top ? top : n);
+    while (n > 0 && !le_pos(p.grid[n], E)) --n;
+    while (n < top && le_pos(p.grid[n + 1], E)) ++n;
+    return n;
+}
+
+// piecewise-linear in E between nodes, constant outside the grid
+template <typename R>
+struct Lookup {
+    int n;
+    R f;
+    int clamp;  // -1 below grid, +1 above, 0 inside
+};
+
+template <typename R>
+__device__ __forceinline__ Lookup<R> locate_energy(const Params<R>& p, R E)
+{
+    Lookup<R> l;
+    l.clamp = 0;
+    if (E <= p.grid[0]) {
+        l.clamp = -1;
+        l.n = 0;
+        l.f = R(0);
+        return l;
+    }
+    if (E >= p.grid[p.n_grid - 1]) {
+        l.clamp = 1;
+        l.n = p.n_grid - 2;
+        l.f = R(0);
+        return l;
+    }
+    l.n = find_bin(p, E);
+    l.f = (E - p.grid[l.n]) / (p.grid[l.n + 1] - p.grid[l.n]);
+    return l;
+}
+
+template <typename R>
+__device__ __forceinline__ R xs_value(const Params<R>& p, const R* t, const Lookup<R>& l, int q)
+{
+    if (l.clamp < 0) return t[q];
+    if (l.clamp > 0) return t[(p.n_grid - 1) * kNq + q];
+    R a = t[l.n * kNq + q], b = t[(l.n + 1) * kNq + q];
+    return a + (b - a) * l.f;
+}
+
+// range: linear through the origin below the grid, linear between nodes,
+// extrapolated with the last slope above
+template <typename R>
+__device__ __forceinline__ R range_value(const Params<R>& p, const R* t, R T, const Lookup<R>& l)
+{
+    if (T < p.grid[0]) return t[3] * (T / p.grid[0]);
+    int n = l.n;
+    R f = l.f;
+    if (l.clamp > 0) f = (T - p.grid[n]) / (p.grid[n + 1] - p.grid[n]);
+    R a = t[n * kNq + 3], b = t[(n + 1) * kNq + 3];
+    return a + (b - a) * f;
+}
+
+// exact inverse of range_value; nstart = bin of the pre-step energy
+// (the answer lies at or below it because r <= R(T))
+template <typename R>
+__device__ __forceinline__ R inv_range(const Params<R>& p, const R* t, R r, int nstart)
+{
+    if (r < t[3]) return p.grid[0] * (r / t[3]);
+    int n = nstart;
+    while (n > 0 && !le_pos(t[n * kNq + 3], r)) --n;
+    int top = p.n_grid - 2;
+    while (n < top && le_pos(t[(n + 1) * kNq + 3], r)) ++n;
+    R a = t[n * kNq + 3], b = t[(n + 1) * kNq + 3];
+    R f = (r - a) / (b - a);
+    return p.grid[n] + (p.grid[n + 1] - p.grid[n]) * f;
+}
+
+// ------------------------------------------------------------------ geometry
+struct Exit {
+    double t;
+    double plane;
+    int next;
+    int axis;
+};
+
+// layer containing z for entries through a side face: largest j with
+// zb[j] <= z, clamped to [0, L-1]
+__device__ __forceinline__ int layer_at(const double* zb, int L, double z)
+{
+    int lo = 0, hi = L - 1;  // answer in [lo, hi]
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (zb[mid] <= z)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// exit parameter t >= 0 along d (any length) from point x in volume vol.
+// Layer: z plane first, then the x and y walls; ties keep the earlier.
+// World vacuum: stack faces (z, x, y) first, then the world walls.
+template <typename R>
+__device__ __forceinline__ Exit nav_exit(const Params<R>& p, int vol, const double x[3], const double d[3])
+{
+    Exit e;
+    e.t = __longlong_as_double(0x7FF0000000000000ll);
+    e.next = kVolOut;
+    e.axis = -1;
+    e.plane = 0.0;
+    if (vol >= 0) {
+        const int L = p.n_layers;
+        if (d[2] > 0.0) {
+            double pl = p.zb[vol + 1];
+            double t = (pl - x[2]) / d[2];
+            if (t < e.t) {
+                e.t = t;
+                e.next = vol + 1 < L ? vol + 1 : kVolWorld;
+                e.axis = 2;
+                e.plane = pl;
+            }
+        } else if (d[2] < 0.0) {
+            double pl = p.zb[vol];
+            double t = (pl - x[2]) / d[2];
+            if (t < e.t) {
+                e.t = t;
+                e.next = vol > 0 ? vol - 1 : kVolWorld;
+                e.axis = 2;
+                e.plane = pl;
+            }
+        }
+        const double half[2] = {p.hx, p.hy};
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            if (d[a] == 0.0) continue;
+            double pl = d[a] > 0.0 ? half[a] : -half[a];
+            double t = (pl - x[a]) / d[a];
+            if (t < e.t) {
+                e.t = t;
+                e.next = kVolWorld;
+                e.axis = a;
+                e.plane = pl;
+            }
+        }
+    } else {
+        const double lo[3] = {-p.hx, -p.hy, p.zb[0]};
+        const double hi[3] = {p.hx, p.hy, p.zb[p.n_layers]};
+        const int order[3] = {2, 0, 1};
+#pragma unroll
+        for (int oi = 0; oi < 3; ++oi) {
+            int a = order[oi];
+            if (d[a] == 0.0) continue;
+            double pl = d[a] > 0.0 ? lo[a] : hi[a];
+            double t = (pl - x[a]) / d[a];
+            if (!(t >= 0.0) || !(t < e.t)) continue;
+            bool ok = true;
+            double qz = 0.0;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                if (b == a) continue;
+                double qb = x[b] + t * d[b];
+                if (qb < lo[b] || qb > hi[b]) ok = false;
+                if (b == 2) qz = qb;
+            }
+            if (!ok) continue;
+            e.t = t;
+            e.axis = a;
+            e.plane = pl;
+            if (a == 2)
+                e.next = d[2] > 0.0 ? 0 : p.n_layers - 1;
+            else
+                e.next = layer_at(p.zb, p.n_layers, qz);
+        }
+#pragma unroll
+        for (int oi = 0; oi < 3; ++oi) {
+            int a = order[oi];
+            if (d[a] == 0.0) continue;
+            double pl = d[a] > 0.0 ? p.whi[a] : p.wlo[a];
+            double t = (pl - x[a]) / d[a];
+            if (t < e.t) {
+                e.t = t;
+                e.next = kVolOut;
+                e.axis = a;
+                e.plane = pl;
+            }
+        }
+    }
+    if (e.t < 0.0) e.t = 0.0;
+    return e;
+}
+
+// ------------------------------------------------------------------ field
+// classical RK4 in path length on (x, u), du/ds = kq u x B, |p| fixed
+// during the step; u renormalised after each substep
+template <typename R>
+__device__ __forceinline__ void rk4(const Params<R>& p, double kq, const double x[3], const double u[3], double hs,
+                                    double xo[3], double uo[3])
+{
+    const double* B = p.B;
+    double a1[3], a2[3], a3[3], a4[3], u2[3], u3[3], u4[3];
+    a1[0] = kq * (u[1] * B[2] - u[2] * B[1]);
+    a1[1] = kq * (u[2] * B[0] - u[0] * B[2]);
+    a1[2] = kq * (u[0] * B[1] - u[1] * B[0]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) u2[i] = u[i] + 0.5 * hs * a1[i];
+    a2[0] = kq * (u2[1] * B[2] - u2[2] * B[1]);
+    a2[1] = kq * (u2[2] * B[0] - u2[0] * B[2]);
+    a2[2] = kq * (u2[0] * B[1] - u2[1] * B[0]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) u3[i] = u[i] + 0.5 * hs * a2[i];
+    a3[0] = kq * (u3[1] * B[2] - u3[2] * B[1]);
+    a3[1] = kq * (u3[2] * B[0] - u3[0] * B[2]);
+    a3[2] = kq * (u3[0] * B[1] - u3[1] * B[0]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) u4[i] = u[i] + hs * a3[i];
+    a4[0] = kq * (u4[1] * B[2] - u4[2] * B[1]);
+    a4[1] = kq * (u4[2] * B[0] - u4[0] * B[2]);
+    a4[2] = kq * (u4[0] * B[1] - u4[1] * B[0]);
+    double h6 = hs / 6.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        xo[i] = x[i] + h6 * (u[i] + 2.0 * u2[i] + 2.0 * u3[i] + u4[i]);
+        uo[i] = u[i] + h6 * (a1[i] + 2.0 * a2[i] + 2.0 * a3[i] + a4[i]);
+    }
+    double n = sqrt(uo[0] * uo[0] + uo[1] * uo[1] + uo[2] * uo[2]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) uo[i] = uo[i] / n;
+}
+
+// substeps of equal length smax/ceil(smax/hmax), hmax = sqrt(8 r delta);
+// the chord of each substep is tested against the current volume and a
+// crossing at fraction f repeats the substep with h f, snapped onto the
+// plane.  Returns the path length.
+template <typename R>
+__device__ __forceinline__ double propagate_field(const Params<R>& p, int charge, double T, int vol, double x[3],
+                                                  double u[3], double smax, Exit* bnd, bool* crossed)
+{
+    double pm = sqrt(T * (T + 2.0 * kMe));
+    double kq = charge * kFieldC / pm;
+    double r = pm / (kFieldC * p.bmag);
+    double hmax = sqrt(8.0 * r * p.rk_delta);
+    double ns = ceil(smax / hmax);
+    if (ns < 1.0) ns = 1.0;
+    double hs = smax / ns;
+    long long n = (long long)ns;
+    double s = 0.0;
+    *crossed = false;
+    for (long long i = 0; i < n; ++i) {
+        double x1[3], u1[3], c[3];
+        rk4(p, kq, x, u, hs, x1, u1);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) c[a] = x1[a] - x[a];
+        Exit e = nav_exit(p, vol, x, c);
+        if (e.t <= 1.0) {
+            double h2 = hs * e.t;
+            rk4(p, kq, x, u, h2, x1, u1);
+            x1[e.axis] = e.plane;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                x[a] = x1[a];
+                u[a] = u1[a];
+            }
+            s += h2;
+            *bnd = e;
+            *crossed = true;
+            return s;
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            x[a] = x1[a];
+            u[a] = u1[a];
+        }
+        s += hs;
+    }
+    return s;
+}
+
+// ------------------------------------------------------------------ kinematics
+// rotate (sin t cos phi, sin t sin phi, cos t), given in the frame whose z
+// axis is u, into the global frame
+template <typename R>
+__device__ __forceinline__ void rotate(const R u[3], R cost, R phi, R out[3])
+{
+    R sint = msqrt(mfmax(R(0), (R(1) - cost) * (R(1) + cost)));
+    R a = sint * mcos(phi);
+    R b = sint * msin(phi);
+    R perp2 = u[0] * u[0] + u[1] * u[1];
+    if (perp2 > R(1e-20)) {
+        R up = msqrt(perp2);
+        out[0] = (u[0] * u[2] * a - u[1] * b) / up + u[0] * cost;
+        out[1] = (u[1] * u[2] * a + u[0] * b) / up + u[1] * cost;
+        out[2] = -up * a + u[2] * cost;
+    } else if (u[2] >= R(0)) {
+        out[0] = a;
+        out[1] = b;
+        out[2] = cost;
+    } else {
+        out[0] = -a;
+        out[1] = b;
+        out[2] = -cost;
+    }
+}
+
+// out = normalize(pa da - pb db); false if the difference vanishes
+template <typename R>
+__device__ __forceinline__ bool momentum_balance(R pa, const R da[3], R pb, const R db[3], R out[3])
+{
+    R v0 = pa * da[0] - pb * db[0];
+    R v1 = pa * da[1] - pb * db[1];
+    R v2 = pa * da[2] - pb * db[2];
+    R n = msqrt(v0 * v0 + v1 * v1 + v2 * v2);
+    if (!(n > R(0))) return false;
+    out[0] = v0 / n;
+    out[1] = v1 / n;
+    out[2] = v2 / n;
+    return true;
+}
+
+// ------------------------------------------------------------------ samplers
+// Products of one interaction: up to two secondaries; `local` is energy
+// deposited on the spot (binding energy).
+template <typename R>
+struct Products {
+    int n;
+    int type[2];
+    R T[2];
+    R dir[2][3];
+    R local;
+    bool parent_alive;
+};
+
+// Compton (Klein-Nishina): composition of the 1/eps and eps densities on
+// [eps0, 1], eps0 = 1/(1 + 2 kappa), weights ln(1/eps0) and (1 - eps0^2)/2,
+// rejection g = 1 - eps sin^2 / (1 + eps^2) (Butcher & Messel 1960).
+template <typename R>
+__device__ __forceinline__ void sample_compton(Draws& d, R k, R dir[3], Products<R>& out, R& knew)
+{
+    const R me = R(kMe);
+    R kappa = k / me;
+    R eps0 = R(1) / (R(1) + R(2) * kappa);
+    R eps0sq = eps0 * eps0;
+    R a1 = -mlog(eps0);
+    R a2 = R(0.5) * (R(1) - eps0sq);
+    R eps, epssq, onecost, sint2, g;
+    for (int trial = 1;; ++trial) {
+        R u1 = draw<R>(d), u2 = draw<R>(d), u3 = draw<R>(d);
+        if (a1 / (a1 + a2) > u1) {
+            eps = mexp(-a1 * u2);
+            epssq = eps * eps;
+        } else {
+            epssq = eps0sq + (R(1) - eps0sq) * u2;
+            eps = msqrt(epssq);
+        }
+        onecost = (R(1) - eps) / (eps * kappa);
+        sint2 = onecost * (R(2) - onecost);
+        g = R(1) - eps * sint2 / (R(1) + epssq);
+        if (u3 <= g || trial >= kMaxTrials) break;
+    }
+    R phi = R(2.0 * kPi) * draw<R>(d);
+    R cost = R(1) - onecost;
+    R kp = eps * k;
+    R gdir[3];
+    rotate(dir, cost, phi, gdir);
+    out.n = 0;
+    R Te = k - kp;
+    R edir[3];
+    if (Te > R(0) && momentum_balance(k, dir, kp, gdir, edir)) {
+        out.type[0] = 1;
+        out.T[0] = Te;
+        out.dir[0][0] = edir[0];
+        out.dir[0][1] = edir[1];
+        out.dir[0][2] = edir[2];
+        out.n = 1;
+    } else {
+        out.local += Te;
+    }
+    dir[0] = gdir[0];
+    dir[1] = gdir[1];
+    dir[2] = gdir[2];
+    knew = kp;
+    out.parent_alive = true;
+}
+
+// Bethe-Heitler, complete screening: x = E(e-)/k uniform on
+// [me/k, 1 - me/k], accepted with 1 - 4/3 x (1 - x); leptons collinear
+template <typename R>
+__device__ __forceinline__ void sample_pair(Draws& d, R k, const R dir[3], Products<R>& out)
+{
+    const R me = R(kMe);
+    R eps0 = me / k;
+    R w = R(1) - R(2) * eps0;
+    R x;
+    for (int trial = 1;; ++trial) {
+        R u1 = draw<R>(d), u2 = draw<R>(d);
+        x = eps0 + w * u1;
+        R f = R(1) - R(4.0 / 3.0) * x * (R(1) - x);
+        if (u2 <= f || trial >= kMaxTrials) break;
+    }
+    R Tm = x * k - me;
+    if (Tm < R(0)) Tm = R(0);
+    R Tp = (k - Tm) - R(2) * me;
+    if (Tp < R(0)) Tp = R(0);
+    out.n = 2;
+    out.type[0] = 1;
+    out.T[0] = Tm;
+    out.type[1] = 2;
+    out.T[1] = Tp;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        out.dir[0][a] = dir[a];
+        out.dir[1][a] = dir[a];
+    }
+    out.parent_alive = false;
+}
+
+// photoelectric stand-in: photoelectron T = k - bk along the photon
+template <typename R>
+__device__ __forceinline__ void sample_photo(R k, R bk, const R dir[3], Products<R>& out)
+{
+    out.n = 1;
+    out.type[0] = 1;
+    out.T[0] = k - bk;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) out.dir[0][a] = dir[a];
+    out.local += bk;
+    out.parent_alive = false;
+}
+
+// bremsstrahlung (Tsai complete screening): k = kc (T/kc)^u, accepted with
+// (4/3 - 4/3 y + y^2) / (4/3), y = k/E; photon along the lepton
+template <typename R>
+__device__ __forceinline__ void sample_brems(Draws& d, R T, R kc, const R dir[3], Products<R>& out, R& Tnew)
+{
+    R E = T + R(kMe);
+    R lr = mlog(T / kc);
+    R k;
+    for (int trial = 1;; ++trial) {
+        R u1 = draw<R>(d), u2 = draw<R>(d);
+        k = kc * mexp(u1 * lr);
+        R y = k / E;
+        R f = R(4.0 / 3.0) - R(4.0 / 3.0) * y + y * y;
+        if (u2 * R(4.0 / 3.0) <= f || trial >= kMaxTrials) break;
+    }
+    out.n = 1;
+    out.type[0] = 0;
+    out.T[0] = k;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) out.dir[0][a] = dir[a];
+    Tnew = T - k;
+    out.parent_alive = true;
+}
+
+// delta ray at cos = sqrt(Td (T + 2me) / (T (Td + 2me))); parent by
+// momentum balance
+template <typename R>
+__device__ __forceinline__ void delta_kinematics(Draws& d, R T, R Td, R dir[3], Products<R>& out, R& Tnew)
+{
+    const R me = R(kMe);
+    R cost = msqrt(Td * (T + R(2) * me) / (T * (Td + R(2) * me)));
+    if (cost > R(1)) cost = R(1);
+    R phi = R(2.0 * kPi) * draw<R>(d);
+    R ddir[3];
+    rotate(dir, cost, phi, ddir);
+    R p0 = msqrt(T * (T + R(2) * me));
+    R pd = msqrt(Td * (Td + R(2) * me));
+    R ndir[3];
+    if (momentum_balance(p0, dir, pd, ddir, ndir)) {
+        dir[0] = ndir[0];
+        dir[1] = ndir[1];
+        dir[2] = ndir[2];
+    }
+    out.n = 1;
+    out.type[0] = 1;
+    out.T[0] = Td;
+    out.dir[0][0] = ddir[0];
+    out.dir[0][1] = ddir[1];
+    out.dir[0][2] = ddir[2];
+    Tnew = T - Td;
+    out.parent_alive = true;
+}
+
+// Moller: eps = xc / (1 - u (1 - 2 xc)) (1/eps^2 envelope on [xc, 1/2]),
+// accepted with eps^2 B(eps) / (2 + g1^2/4)
+template <typename R>
+__device__ __forceinline__ void sample_moller(Draws& d, R T, R cut, R dir[3], Products<R>& out, R& Tnew)
+{
+    const R me = R(kMe);
+    R xc = cut / T;
+    R g = (T + me) / me;
+    R g1 = (g - R(1)) / g;
+    R c = (R(2) * g - R(1)) / (g * g);
+    R gmax = R(2) + R(0.25) * g1 * g1;
+    R eps;
+    for (int trial = 1;; ++trial) {
+        R u1 = draw<R>(d), u2 = draw<R>(d);
+        eps = xc / (R(1) - u1 * (R(1) - R(2) * xc));
+        R q = eps / (R(1) - eps);
+        R f = R(1) + q * q + g1 * g1 * eps * eps - c * q;
+        if (u2 * gmax <= f || trial >= kMaxTrials) break;
+    }
+    delta_kinematics(d, T, eps * T, dir, out, Tnew);
+}
+
+// Bhabha: eps = xc / (1 - u (1 - xc)) (1/eps^2 envelope on [xc, 1]),
+// accepted with beta^2 eps^2 times the bracket of dsigma/deps (<= 1)
+template <typename R>
+__device__ __forceinline__ void sample_bhabha(Draws& d, R T, R cut, R dir[3], Products<R>& out, R& Tnew)
+{
+    const R me = R(kMe);
+    R xc = cut / T;
+    R g = (T + me) / me;
+    R y = R(1) / (g + R(1));
+    R y2 = y * y;
+    R t = R(1) - R(2) * y;
+    R b2 = T * (T + R(2) * me) / ((T + me) * (T + me));
+    R c1 = R(2) - y2;
+    R c2 = t * (R(3) + y2);
+    R c4 = t * t * t;
+    R c3 = t * t + c4;
+    R eps;
+    for (int trial = 1;; ++trial) {
+        R u1 = draw<R>(d), u2 = draw<R>(d);
+        eps = xc / (R(1) - u1 * (R(1) - xc));
+        R f = R(1) - b2 * eps * (c1 - eps * (c2 - eps * (c3 - eps * c4)));
+        if (u2 <= f || trial >= kMaxTrials) break;
+    }
+    delta_kinematics(d, T, eps * T, dir, out, Tnew);
+}
+
+// two-photon annihilation in flight (Heitler): eps = emin (emax/emin)^u
+// (1/eps envelope), accepted with 1 - ((g+1)^2 eps + 1/eps)/(g^2 + 4g + 1);
+// photon 1 at cos = (T + 2me)(E1 - me)/(p E1), photon 2 by momentum balance
+template <typename R>
+__device__ __forceinline__ void sample_annih(Draws& d, R T, const R dir[3], Products<R>& out)
+{
+    const R me = R(kMe);
+    R tau = T / me;
+    R g = tau + R(1);
+    R a = tau + R(2);
+    R s = msqrt(tau * (tau + R(2)));
+    R emin = R(0.5) * (R(1) - s / a);
+    R emax = R(1) - emin;
+    R lr = mlog(emax / emin);
+    R bq = g * g + R(4) * g + R(1);
+    R eps;
+    for (int trial = 1;; ++trial) {
+        R u1 = draw<R>(d), u2 = draw<R>(d);
+        eps = emin * mexp(u1 * lr);
+        R f = R(1) - (a * a * eps + R(1) / eps) / bq;
+        if (u2 <= f || trial >= kMaxTrials) break;
+    }
+    R Etot = T + R(2) * me;
+    R E1 = eps * Etot;
+    R E2 = Etot - E1;
+    R pm = msqrt(T * (T + R(2) * me));
+    R cost = Etot * (E1 - me) / (pm * E1);
+    if (cost > R(1)) cost = R(1);
+    if (cost < R(-1)) cost = R(-1);
+    R phi = R(2.0 * kPi) * draw<R>(d);
+    R d1[3], d2[3];
+    rotate(dir, cost, phi, d1);
+    if (!momentum_balance(pm, dir, E1, d1, d2)) {
+        d2[0] = -d1[0];
+        d2[1] = -d1[1];
+        d2[2] = -d1[2];
+    }
+    out.n = 2;
+    out.type[0] = 0;
+    out.T[0] = E1;
+    out.type[1] = 0;
+    out.T[1] = E2;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        out.dir[0][a] = d1[a];
+        out.dir[1][a] = d2[a];
+    }
+    out.parent_alive = false;
+}
+
+}  // namespace emt

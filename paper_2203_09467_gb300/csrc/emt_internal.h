@@ -1,0 +1,47 @@
+// emt_internal.h -- declarations shared by the library's translation units
+// (host runtime, table builder, FP64 and mixed-precision step kernels).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "emt_device.cuh"
+
+namespace emt {
+
+struct MaterialDev {
+    double Z, A, rho, I_eV, bk;
+};
+
+struct TableBuild {
+    const MaterialDev* mats;  // device
+    int n_mat;
+    int n_grid;
+    int bpd;
+    double e_lo;
+    double cut[3];
+    unsigned mask;
+    double* grid;  // [n_grid]
+    double* tab;   // [n_mat][3][n_grid][4]
+    double* dedx;  // [n_mat][3][n_grid]
+    float* tabf;   // optional float copies (mixed precision)
+    float* gridf;
+};
+
+// scratch: (32 + n_mat * 2 * n_grid) doubles
+cudaError_t build_tables(const TableBuild& b, double* scratch, cudaStream_t st);
+
+template <typename R>
+struct Launch {
+    static cudaError_t step(const Params<R>& p, int side, int cin, int cout, int cclr, int grid, int block,
+                            cudaStream_t st);
+    static cudaError_t admit(const Params<R>& p, int side, int cs, int n, const int32_t* ev, const int32_t* type,
+                             const double* T, const double* pos, const double* dir, const uint32_t* slot_of_event,
+                             const uint32_t* uid_of, cudaStream_t st);
+    static cudaError_t set_tracks(const Params<R>& p, int side, int cs, int n, const double* rec,
+                                  const uint64_t* uid, const int32_t* slot, cudaStream_t st);
+    static cudaError_t get_tracks(const Params<R>& p, int side, int nG, int nC, double* rec, uint64_t* uid,
+                                  int32_t* slot, cudaStream_t st);
+    static int max_blocks_per_sm(int block);
+};
+
+}  // namespace emt

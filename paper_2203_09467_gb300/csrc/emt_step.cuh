@@ -1,0 +1,586 @@
+// emt_step.cuh -- one transport step of every track in flight, as one
+// kernel launch (arXiv:2203.09467 Sec. 3.1: one thread per track; Sec. 3.2:
+// cross sections, continuous loss, discrete interactions, secondaries and
+// cutoffs; Sec. 3.3: propagation; Sec. 3.4: scoring in kernels).
+//
+// Layout and scheduling (the paper's own design launches one kernel per
+// model from the host; this one is GB300-first):
+//  * Tracks live in two ping-pong structure-of-arrays buffers of Q slots.
+//    Photons fill the front of a buffer, charged tracks the back, so one
+//    step reads a dense, coalesced range per particle type and writes the
+//    survivors and secondaries compactly into the other buffer: the step
+//    is also the compaction and the particle-type partition.
+//  * Work is handed out in chunks of blockDim.x tracks of one particle type
+//    by an atomic dispenser, so every warp runs the photon or the charged
+//    code path only, and blocks stay busy until the step is drained.
+//  * Output slots are reserved once per warp: a shuffle prefix sum over the
+//    lanes' photon and charged output counts and one atomicAdd per type.
+//  * Capacity: at most n + 2p outputs come from n inputs of which p are
+//    stepped, so p = min(n, (Q - n)/2) tracks step and the rest are copied
+//    unchanged (deferred).  A deferred track keeps its step counter, so its
+//    random stream and therefore every result are unchanged (the paper's
+//    out-of-memory robustness without loss of reproducibility, Sec. 3.1).
+#pragma once
+
+#include "emt_device.cuh"
+
+namespace emt {
+
+template <typename R>
+struct TrackReg {
+    double x[3];
+    R u[3];
+    R T;
+    uint64_t uid;
+    uint32_t ev;
+    uint32_t step;
+    int type;
+    int vol;
+};
+
+// outputs of one input track: survivor first, then secondaries; all share
+// the post-step position, event and volume
+template <typename R>
+struct StepOut {
+    int n;
+    int type[3];
+    R T[3];
+    R u[3][3];
+    uint64_t uid[3];
+    uint32_t step[3];
+};
+
+template <typename R>
+__device__ __forceinline__ void deposit(const Params<R>& p, uint32_t ev, int vol, double e)
+{
+    if (e == 0.0) return;
+    int col = p.n_bins;
+    if (vol >= 0) {
+        int b = p.lbin[vol];
+        if (b >= 0 && b < p.n_bins) col = b;
+    }
+    atomicAdd(&p.hist[(size_t)ev * p.hstride + col], e);
+}
+
+__device__ __forceinline__ double rest_energy(int type) { return type == 2 ? 2.0 * kMe : 0.0; }
+
+template <typename R>
+__device__ __forceinline__ void finish_track(const Params<R>& p, uint32_t ev, uint32_t steps)
+{
+    atomicAdd(&p.counts[2 * (size_t)ev + 0], (unsigned long long)steps);
+    atomicAdd(&p.counts[2 * (size_t)ev + 1], 1ull);
+}
+
+// An event is finished when its live-track count reaches zero.  A thread
+// adds its secondaries before removing its own track, so the count of an
+// event cannot touch zero while one of its tracks is still alive.
+template <typename R>
+__device__ __forceinline__ void update_live(const Params<R>& p, uint32_t ev, int delta)
+{
+    if (delta == 0) return;
+    int old = atomicAdd(&p.live[ev], delta);
+    if (old + delta == 0) {
+        unsigned k = atomicAdd(p.done_head, 1u);
+        p.done_ring[k % (unsigned)p.max_events] = ev;
+    }
+}
+
+// One step of one track; the order is
+//  1 cross sections at the pre-step energy   2 s_int = -ln(u0)/Sigma_tot
+//  3 e+-: s_max = max(f R, min(R, r_final))  4 s_phys = min
+//  5 propagate to min(s_phys, boundary), ties to the boundary
+//  6 e+-: T' = R^-1(R(T) - s), deposit T - T'
+//  7 e+- below the cut: deposit T' (+2 me for e+), track ends
+//  8 boundary: logical volume update; leaving the world tallies escape
+//  9 interaction: process by u1 Sigma_tot against the cumulative pre-step
+//    Sigma's, sampled with the post-loss energy
+// 10 step += 1; at max_steps the track is killed
+template <typename R>
+__device__ __forceinline__ void step_track(const Params<R>& p, TrackReg<R>& t, StepOut<R>& o)
+{
+    o.n = 0;
+    const uint64_t event_id = p.event_id[t.ev];
+    Draws dr;
+    dr.init(p.seed, event_id, t.uid, t.step);
+    const int mi = t.vol >= 0 ? p.lmat[t.vol] : -1;
+    const bool matter = mi >= 0 && !p.vacuum[mi];
+    const bool charged = t.type != 0;
+    const int nproc = t.type == 1 ? 2 : 3;
+    const R* tab = matter ? p.tab + (size_t)(mi * 3 + t.type) * p.n_grid * kNq : nullptr;
+
+    R sig[3] = {R(0), R(0), R(0)};
+    R sig_tot = R(0);
+    R Rng = R(0);
+    Lookup<R> lk;
+    lk.n = 0;
+    lk.f = R(0);
+    lk.clamp = -1;
+    if (matter) {
+        lk = locate_energy(p, t.T);
+        sig[0] = xs_value(p, tab, lk, 0);
+        sig[1] = xs_value(p, tab, lk, 1);
+        sig_tot = sig[0] + sig[1];
+        if (nproc == 3) {
+            sig[2] = xs_value(p, tab, lk, 2);
+            sig_tot = sig_tot + sig[2];
+        }
+    }
+    const R kInf = R(__longlong_as_double(0x7FF0000000000000ll));
+    R s_int = kInf;
+    if (sig_tot > R(0)) {
+        dr.next = 0;
+        s_int = -mlog(draw<R>(dr)) / sig_tot;
+    }
+    R s_max = kInf;
+    if (charged && matter) {
+        Rng = range_value(p, tab, t.T, lk);
+        R fr_lim = R(p.final_range);
+        R lim = Rng < fr_lim ? Rng : fr_lim;
+        R fr = R(p.step_frac) * Rng;
+        s_max = fr > lim ? fr : lim;
+    }
+    R s_phys = s_max;
+    bool interact = false;
+    if (s_int < s_max) {
+        s_phys = s_int;
+        interact = true;
+    }
+
+    // 5: propagation (positions and boundary distances in FP64)
+    double s;
+    bool boundary = false;
+    Exit e;
+    double ud[3] = {(double)t.u[0], (double)t.u[1], (double)t.u[2]};
+    if (!(charged && p.has_field)) {
+        e = nav_exit(p, t.vol, t.x, ud);
+        if (e.t <= (double)s_phys) {
+            s = e.t;
+            boundary = true;
+        } else {
+            s = (double)s_phys;
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) t.x[a] = t.x[a] + s * ud[a];
+        if (boundary && e.axis >= 0) t.x[e.axis] = e.plane;
+    } else {
+        double smax = (double)s_phys;
+        if (smax > p.max_field_step) {
+            smax = p.max_field_step;
+            interact = false;
+        }
+        bool crossed = false;
+        s = propagate_field(p, t.type == 1 ? -1 : 1, (double)t.T, t.vol, t.x, ud, smax, &e, &crossed);
+        boundary = crossed;
+        t.u[0] = R(ud[0]);
+        t.u[1] = R(ud[1]);
+        t.u[2] = R(ud[2]);
+    }
+    if (boundary) interact = false;
+
+    bool alive = true;
+    // 6-7: continuous loss
+    if (charged && matter) {
+        R r = Rng - R(s);
+        R Tn = r > R(0) ? inv_range(p, tab, r, lk.n) : R(0);
+        R ed = t.T - Tn;
+        deposit(p, t.ev, t.vol, (double)ed);
+        t.T = Tn;
+        if (t.T < R(p.cut[t.type])) {
+            deposit(p, t.ev, t.vol, (double)t.T + rest_energy(t.type));
+            alive = false;
+        }
+    }
+    int nsec = 0;
+    int sec_type[2];
+    R sec_T[2];
+    R sec_u[2][3];
+    int sec_k[2];
+    // 8: boundary
+    if (alive && boundary) {
+        t.vol = e.next;
+        if (t.vol == kVolOut) {
+            atomicAdd(&p.ledger[3 * (size_t)t.ev + 0], (double)t.T + rest_energy(t.type));
+            alive = false;
+        }
+    } else if (alive && interact) {
+        // 9: select and sample
+        dr.next = 1;
+        R xsel = draw<R>(dr) * sig_tot;
+        int proc = nproc - 1;
+        R c = R(0);
+        for (int i = 0; i < nproc; ++i) {
+            c += sig[i];
+            if (xsel < c) {
+                proc = i;
+                break;
+            }
+        }
+        dr.next = 2;
+        Products<R> pr;
+        pr.n = 0;
+        pr.local = R(0);
+        pr.parent_alive = true;
+        bool null_interaction = false;
+        const R T = t.T;
+        const R cut_e = R(p.cut[1]), kc = R(p.cut[0]);
+        if (t.type == 0) {
+            if (proc == 0) {
+                R bk = R(p.bk[mi]);
+                if (T > bk)
+                    sample_photo(T, bk, t.u, pr);
+                else
+                    null_interaction = true;
+            } else if (proc == 1) {
+                sample_compton(dr, T, t.u, pr, t.T);
+            } else {
+                if (T > R(2.0 * kMe))
+                    sample_pair(dr, T, t.u, pr);
+                else
+                    null_interaction = true;
+            }
+        } else if (proc == 0) {
+            if (t.type == 1) {
+                if (T > R(2) * cut_e)
+                    sample_moller(dr, T, cut_e, t.u, pr, t.T);
+                else
+                    null_interaction = true;
+            } else {
+                if (T > cut_e)
+                    sample_bhabha(dr, T, cut_e, t.u, pr, t.T);
+                else
+                    null_interaction = true;
+            }
+        } else if (proc == 1) {
+            if (T > kc)
+                sample_brems(dr, T, kc, t.u, pr, t.T);
+            else
+                null_interaction = true;
+        } else {
+            sample_annih(dr, T, t.u, pr);
+        }
+        if (pr.local != R(0)) deposit(p, t.ev, t.vol, (double)pr.local);
+        for (int k = 0; k < pr.n; ++k) {
+            int st = pr.type[k];
+            R sT = pr.T[k];
+            if (sT < R(p.cut[st])) {
+                deposit(p, t.ev, t.vol, (double)sT + rest_energy(st));
+                continue;
+            }
+            sec_type[nsec] = st;
+            sec_T[nsec] = sT;
+            sec_u[nsec][0] = pr.dir[k][0];
+            sec_u[nsec][1] = pr.dir[k][1];
+            sec_u[nsec][2] = pr.dir[k][2];
+            sec_k[nsec] = k;
+            ++nsec;
+        }
+        if (!null_interaction) {
+            if (!pr.parent_alive) {
+                alive = false;
+            } else if (t.T < R(p.cut[t.type])) {
+                deposit(p, t.ev, t.vol, (double)t.T + rest_energy(t.type));
+                alive = false;
+            }
+        }
+    }
+    // 10
+    const uint32_t parent_step = t.step;
+    t.step += 1;
+    if (alive && (int)t.step >= p.max_steps) {
+        atomicAdd(&p.ledger[3 * (size_t)t.ev + 1], (double)t.T + rest_energy(t.type));
+        alive = false;
+    }
+    if (alive) {
+        o.type[0] = t.type;
+        o.T[0] = t.T;
+        o.u[0][0] = t.u[0];
+        o.u[0][1] = t.u[1];
+        o.u[0][2] = t.u[2];
+        o.uid[0] = t.uid;
+        o.step[0] = t.step;
+        o.n = 1;
+    } else {
+        finish_track(p, t.ev, t.step);
+    }
+    for (int k = 0; k < nsec; ++k) {
+        int j = o.n;
+        o.type[j] = sec_type[k];
+        o.T[j] = sec_T[k];
+        o.u[j][0] = sec_u[k][0];
+        o.u[j][1] = sec_u[k][1];
+        o.u[j][2] = sec_u[k][2];
+        o.uid[j] = child_uid(p.seed, event_id, t.uid, parent_step, (uint32_t)sec_k[k]);
+        o.step[j] = 0;
+        o.n = j + 1;
+    }
+    update_live(p, t.ev, nsec - (alive ? 0 : 1));
+}
+
+template <typename R>
+__device__ __forceinline__ void load_track(const Tracks<R>& q, long long i, TrackReg<R>& t)
+{
+    t.x[0] = q.x[i];
+    t.x[1] = q.y[i];
+    t.x[2] = q.z[i];
+    t.u[0] = q.ux[i];
+    t.u[1] = q.uy[i];
+    t.u[2] = q.uz[i];
+    t.T = q.T[i];
+    t.uid = q.uid[i];
+    t.ev = q.ev[i];
+    t.step = q.step[i];
+    uint32_t tv = q.tv[i];
+    t.type = tv_type(tv);
+    t.vol = tv_vol(tv);
+}
+
+template <typename R>
+__device__ __forceinline__ void store_track(const Tracks<R>& q, long long i, const double x[3], const R u[3], R T,
+                                            uint64_t uid, uint32_t ev, uint32_t step, int type, int vol)
+{
+    q.x[i] = x[0];
+    q.y[i] = x[1];
+    q.z[i] = x[2];
+    q.ux[i] = u[0];
+    q.uy[i] = u[1];
+    q.uz[i] = u[2];
+    q.T[i] = T;
+    q.uid[i] = uid;
+    q.ev[i] = ev;
+    q.step[i] = step;
+    q.tv[i] = pack_tv(type, vol);
+}
+
+// One step-loop iteration over both particle queues of side `side`.
+// Counter slots: cin = this step's input counts (and chunk dispenser),
+// cout = output counts (zero on entry), cclr = slot cleared for the next
+// step (it held the previous step's input).
+template <typename R>
+__global__ void __launch_bounds__(256) k_step(Params<R> p, int side, int cin, int cout, int cclr)
+{
+    __shared__ int s_chunk;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        p.cnt[cclr].n[0] = 0;
+        p.cnt[cclr].n[1] = 0;
+        p.cnt[cclr].work = 0;
+        p.cnt[cclr].deferred = 0;
+    }
+    const Tracks<R> qi = p.q[side];
+    const Tracks<R> qo = p.q[side ^ 1];
+    const int nG = p.cnt[cin].n[0];
+    const int nC = p.cnt[cin].n[1];
+    const long long Q = p.Q;
+    const long long ntot = (long long)nG + nC;
+    long long pmax = (Q - ntot) / 2;
+    if (pmax < 0) pmax = 0;
+    const long long pC = nC < pmax ? nC : pmax;
+    const long long pG = nG < pmax - pC ? nG : pmax - pC;
+    const int bs = blockDim.x;
+    const int chunksG = (nG + bs - 1) / bs;
+    const int chunksC = (nC + bs - 1) / bs;
+    const int lane = threadIdx.x & 31;
+
+    for (;;) {
+        if (threadIdx.x == 0) s_chunk = atomicAdd(&p.cnt[cin].work, 1);
+        __syncthreads();
+        const int chunk = s_chunk;
+        __syncthreads();
+        if (chunk >= chunksG + chunksC) break;
+        bool photon_chunk = chunk < chunksG;
+        long long i = photon_chunk ? (long long)chunk * bs + threadIdx.x
+                                   : (long long)(chunk - chunksG) * bs + threadIdx.x;
+        const long long n_here = photon_chunk ? nG : nC;
+        const bool active = i < n_here;
+        const bool stepping = active && i < (photon_chunk ? pG : pC);
+        const long long src = photon_chunk ? i : Q - nC + i;
+        if (threadIdx.x == 0) {
+            long long lim = photon_chunk ? pG : pC;
+            long long c0 = photon_chunk ? (long long)chunk * bs : (long long)(chunk - chunksG) * bs;
+            long long c1 = c0 + bs < lim ? c0 + bs : lim;
+            long long e1 = c0 + bs < n_here ? c0 + bs : n_here;
+            if (c1 > c0) atomicAdd(&p.total_steps[0], (unsigned long long)(c1 - c0));
+            long long nd = e1 - (c1 > c0 ? c1 : c0);
+            if (nd > 0) atomicAdd(&p.total_steps[1], (unsigned long long)nd);
+        }
+
+        TrackReg<R> t;
+        StepOut<R> o;
+        o.n = 0;
+        if (active) {
+            load_track(qi, src, t);
+            if (stepping) {
+                step_track(p, t, o);
+            } else {
+                o.n = 1;
+                o.type[0] = t.type;
+                o.T[0] = t.T;
+                o.u[0][0] = t.u[0];
+                o.u[0][1] = t.u[1];
+                o.u[0][2] = t.u[2];
+                o.uid[0] = t.uid;
+                o.step[0] = t.step;
+            }
+        }
+        // warp-aggregated reservation: counts packed as g | c << 16
+        int ng = 0, nc = 0;
+        for (int k = 0; k < o.n; ++k) {
+            if (o.type[k] == 0)
+                ++ng;
+            else
+                ++nc;
+        }
+        int v = ng | (nc << 16);
+        int incl = v;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            int y = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        int excl = incl - v;
+        int tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        int baseG = 0, baseC = 0;
+        if (lane == 31) {
+            int tg = tot & 0xFFFF, tc = tot >> 16;
+            if (tg) baseG = atomicAdd(&p.cnt[cout].n[0], tg);
+            if (tc) baseC = atomicAdd(&p.cnt[cout].n[1], tc);
+        }
+        baseG = __shfl_sync(0xFFFFFFFFu, baseG, 31);
+        baseC = __shfl_sync(0xFFFFFFFFu, baseC, 31);
+        long long og = (long long)baseG + (excl & 0xFFFF);
+        long long oc = (long long)baseC + (excl >> 16);
+        for (int k = 0; k < o.n; ++k) {
+            long long dst;
+            if (o.type[k] == 0) {
+                dst = og++;
+            } else {
+                dst = Q - 1 - oc;
+                ++oc;
+            }
+            if (dst < 0 || dst >= Q) {
+                atomicOr(p.status, kStatusQueueOverflow);
+                continue;
+            }
+            store_track(qo, dst, t.x, o.u[k], o.T[k], o.uid[k], t.ev, o.step[k], o.type[k], t.vol);
+        }
+    }
+}
+
+// Admit primaries (structure of arrays, device memory) into side `side`,
+// appending after the tracks already counted in slot `cs`.  Primaries
+// below their cut deposit at once; outside the world they escape.
+template <typename R>
+__global__ void k_admit(Params<R> p, int side, int cs, int n, const int32_t* ev, const int32_t* type,
+                        const double* T, const double* pos, const double* dir, const uint32_t* slot_of_event,
+                        const uint32_t* uid_of)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    bool keep = false;
+    TrackReg<R> t;
+    if (i < n) {
+        t.ev = slot_of_event[ev[i]];
+        t.type = type[i];
+        t.T = R(T[i]);
+        t.x[0] = pos[3 * i + 0];
+        t.x[1] = pos[3 * i + 1];
+        t.x[2] = pos[3 * i + 2];
+        t.u[0] = R(dir[3 * i + 0]);
+        t.u[1] = R(dir[3 * i + 1]);
+        t.u[2] = R(dir[3 * i + 2]);
+        t.uid = uid_of[i];
+        t.step = 0;
+        // locate: inside the stack box -> layer; inside the world -> world
+        int vol;
+        if (t.x[0] >= -p.hx && t.x[0] <= p.hx && t.x[1] >= -p.hy && t.x[1] <= p.hy && t.x[2] >= p.zb[0] &&
+            t.x[2] <= p.zb[p.n_layers]) {
+            vol = layer_at(p.zb, p.n_layers, t.x[2]);
+        } else if (t.x[0] < p.wlo[0] || t.x[0] > p.whi[0] || t.x[1] < p.wlo[1] || t.x[1] > p.whi[1] ||
+                   t.x[2] < p.wlo[2] || t.x[2] > p.whi[2]) {
+            vol = kVolOut;
+        } else {
+            vol = kVolWorld;
+        }
+        t.vol = vol;
+        double E = (double)T[i] + rest_energy(t.type);
+        if (t.type < 0 || t.type > 2) {
+            atomicOr(p.status, kStatusBadTrack);
+        } else {
+            atomicAdd(&p.ledger[3 * (size_t)t.ev + 2], E);
+            if (vol == kVolOut) {
+                atomicAdd(&p.ledger[3 * (size_t)t.ev + 0], E);
+            } else if (T[i] < p.cut[t.type]) {
+                deposit(p, t.ev, vol, E);
+            } else {
+                keep = true;
+                atomicAdd(&p.live[t.ev], 1);
+            }
+        }
+    }
+    unsigned mG = __ballot_sync(0xFFFFFFFFu, keep && t.type == 0);
+    unsigned mC = __ballot_sync(0xFFFFFFFFu, keep && t.type != 0);
+    int baseG = 0, baseC = 0;
+    if (lane == 0) {
+        if (mG) baseG = atomicAdd(&p.cnt[cs].n[0], __popc(mG));
+        if (mC) baseC = atomicAdd(&p.cnt[cs].n[1], __popc(mC));
+    }
+    baseG = __shfl_sync(0xFFFFFFFFu, baseG, 0);
+    baseC = __shfl_sync(0xFFFFFFFFu, baseC, 0);
+    if (keep) {
+        unsigned below = (1u << lane) - 1u;
+        long long dst = t.type == 0 ? (long long)baseG + __popc(mG & below)
+                                    : p.Q - 1 - ((long long)baseC + __popc(mC & below));
+        if (dst < 0 || dst >= p.Q) {
+            atomicOr(p.status, kStatusQueueOverflow);
+        } else {
+            store_track(p.q[side], dst, t.x, t.u, t.T, t.uid, t.ev, t.step, t.type, t.vol);
+        }
+    }
+}
+
+// Diagnostics: write explicit track records into side `side`.
+template <typename R>
+__global__ void k_set_tracks(Params<R> p, int side, int cs, int n, const double* rec, const uint64_t* uid,
+                             const int32_t* slot)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double* r = rec + 10 * (size_t)i;
+    int type = (int)r[0];
+    double x[3] = {r[2], r[3], r[4]};
+    R u[3] = {R(r[5]), R(r[6]), R(r[7])};
+    long long dst;
+    if (type == 0)
+        dst = atomicAdd(&p.cnt[cs].n[0], 1);
+    else
+        dst = p.Q - 1 - atomicAdd(&p.cnt[cs].n[1], 1);
+    if (dst < 0 || dst >= p.Q) {
+        atomicOr(p.status, kStatusQueueOverflow);
+        return;
+    }
+    store_track(p.q[side], dst, x, u, R(r[1]), uid[i], (uint32_t)slot[i], (uint32_t)r[9], type, (int)r[8]);
+}
+
+template <typename R>
+__global__ void k_get_tracks(Params<R> p, int side, int nG, int nC, double* rec, uint64_t* uid, int32_t* slot)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nG + nC) return;
+    long long src = i < nG ? i : p.Q - nC + (i - nG);
+    TrackReg<R> t;
+    load_track(p.q[side], src, t);
+    double* r = rec + 10 * (size_t)i;
+    r[0] = t.type;
+    r[1] = (double)t.T;
+    r[2] = t.x[0];
+    r[3] = t.x[1];
+    r[4] = t.x[2];
+    r[5] = (double)t.u[0];
+    r[6] = (double)t.u[1];
+    r[7] = (double)t.u[2];
+    r[8] = t.vol;
+    r[9] = t.step;
+    uid[i] = t.uid;
+    slot[i] = (int32_t)t.ev;
+}
+
+}  // namespace emt
