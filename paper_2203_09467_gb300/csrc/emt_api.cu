@@ -343,6 +343,7 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
     EMT_CUDA(c, cudaMemcpyAsync(c->h_steps, c->pool + pl.total_steps, 16, cudaMemcpyDeviceToHost, c->stream));
     EMT_CUDA(c, cudaStreamSynchronize(c->stream));
     const unsigned long long steps0 = c->h_steps[0], def0 = c->h_steps[1];
+    unsigned long long last_steps = steps0;
     const int64_t live0 = c->live_g + c->live_c;
     int64_t peak = live0;
     double kernel_ms = 0.0;
@@ -353,9 +354,19 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
         float ms = 0.f;
         EMT_CUDA(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
         kernel_ms += ms;
+        const bool same = c->live_g == c->h_cnt->n[0] && c->live_c == c->h_cnt->n[1];
         c->live_g = c->h_cnt->n[0];
         c->live_c = c->h_cnt->n[1];
         peak = std::max<int64_t>(peak, c->live_g + c->live_c);
+        if (same && c->live_g + c->live_c > 0) {
+            // unchanged population: make sure some track advanced
+            EMT_CUDA(c, cudaMemcpyAsync(c->h_steps, c->pool + pl.total_steps, 16, cudaMemcpyDeviceToHost, c->stream));
+            EMT_CUDA(c, cudaStreamSynchronize(c->stream));
+            if (c->h_steps[0] == last_steps)
+                return fail(c, EMT_ERR_CAPACITY,
+                            "no track could advance: slot_capacity is too small for the tracks in flight");
+            last_steps = c->h_steps[0];
+        }
         return EMT_OK;
     };
     auto one_plain = [&]() -> emt_status {
@@ -948,6 +959,8 @@ emt_status emt_debug_set_tracks(emt_ctx* c, int32_t n, const double* rec, const 
             return fail(c, EMT_ERR_INVALID_ARG, "bad track record");
     }
     const Plan& pl = c->plan;
+    r = drain_done(c);  // injected tracks count toward their events again
+    if (r != EMT_OK) return r;
     int cs = (int)(c->it % 3), side = (int)(c->it & 1);
     EMT_CUDA(c, cudaMemsetAsync(c->pool + pl.cnt + sizeof(Counters) * cs, 0, sizeof(Counters), c->stream));
     double* drec = nullptr;

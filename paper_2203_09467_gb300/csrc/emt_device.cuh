@@ -71,7 +71,7 @@ struct Tracks {
 struct Counters {
     int n[2];      // photons, charged
     int work;      // chunk dispenser
-    int deferred;  // tracks copied without stepping
+    int used;      // growth tokens taken (steps with two outputs)
 };
 
 template <typename R>

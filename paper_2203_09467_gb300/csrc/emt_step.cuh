@@ -15,11 +15,11 @@
 //    code path only, and blocks stay busy until the step is drained.
 //  * Output slots are reserved once per warp: a shuffle prefix sum over the
 //    lanes' photon and charged output counts and one atomicAdd per type.
-//  * Capacity: at most n + 2p outputs come from n inputs of which p are
-//    stepped, so p = min(n, (Q - n)/2) tracks step and the rest are copied
-//    unchanged (deferred).  A deferred track keeps its step counter, so its
-//    random stream and therefore every result are unchanged (the paper's
-//    out-of-memory robustness without loss of reproducibility, Sec. 3.1).
+//  * Capacity: a step whose outputs do not fit is discarded and the track
+//    is copied unchanged (deferred, see k_step).  A deferred track keeps its
+//    step counter, so its random stream and every result are unchanged (the
+//    paper's out-of-memory robustness without loss of reproducibility,
+//    Sec. 3.1).
 #pragma once
 
 #include "emt_device.cuh"
@@ -50,8 +50,21 @@ struct StepOut {
     uint32_t step[3];
 };
 
+// Side effects of one step, staged in registers and applied only once the
+// step is committed (a step whose outputs do not fit is discarded and the
+// track is copied unchanged).  Every deposit of a step lands in the volume
+// the track was in before any boundary crossing.
+struct Effects {
+    double dep;   // deposited energy
+    double esc;   // escaped energy
+    double kill;  // energy of a track killed at the step limit
+    int vol;      // volume of the deposits
+    bool finished;
+    int live_delta;
+};
+
 template <typename R>
-__device__ __forceinline__ void deposit(const Params<R>& p, uint32_t ev, int vol, double e)
+__device__ __forceinline__ void deposit_now(const Params<R>& p, uint32_t ev, int vol, double e)
 {
     if (e == 0.0) return;
     int col = p.n_bins;
@@ -96,9 +109,15 @@ __device__ __forceinline__ void update_live(const Params<R>& p, uint32_t ev, int
 //    Sigma's, sampled with the post-loss energy
 // 10 step += 1; at max_steps the track is killed
 template <typename R>
-__device__ __forceinline__ void step_track(const Params<R>& p, TrackReg<R>& t, StepOut<R>& o)
+__device__ __forceinline__ void step_track(const Params<R>& p, TrackReg<R>& t, StepOut<R>& o, Effects& fx)
 {
     o.n = 0;
+    fx.dep = 0.0;
+    fx.esc = 0.0;
+    fx.kill = 0.0;
+    fx.vol = t.vol;
+    fx.finished = false;
+    fx.live_delta = 0;
     const uint64_t event_id = p.event_id[t.ev];
     Draws dr;
     dr.init(p.seed, event_id, t.uid, t.step);
@@ -183,10 +202,10 @@ __device__ __forceinline__ void step_track(const Params<R>& p, TrackReg<R>& t, S
         R r = Rng - R(s);
         R Tn = r > R(0) ? inv_range(p, tab, r, lk.n) : R(0);
         R ed = t.T - Tn;
-        deposit(p, t.ev, t.vol, (double)ed);
+        fx.dep += (double)ed;
         t.T = Tn;
         if (t.T < R(p.cut[t.type])) {
-            deposit(p, t.ev, t.vol, (double)t.T + rest_energy(t.type));
+            fx.dep += (double)t.T + rest_energy(t.type);
             alive = false;
         }
     }
@@ -199,7 +218,7 @@ __device__ __forceinline__ void step_track(const Params<R>& p, TrackReg<R>& t, S
     if (alive && boundary) {
         t.vol = e.next;
         if (t.vol == kVolOut) {
-            atomicAdd(&p.ledger[3 * (size_t)t.ev + 0], (double)t.T + rest_energy(t.type));
+            fx.esc = (double)t.T + rest_energy(t.type);
             alive = false;
         }
     } else if (alive && interact) {
@@ -258,12 +277,12 @@ __device__ __forceinline__ void step_track(const Params<R>& p, TrackReg<R>& t, S
         } else {
             sample_annih(dr, T, t.u, pr);
         }
-        if (pr.local != R(0)) deposit(p, t.ev, t.vol, (double)pr.local);
+        if (pr.local != R(0)) fx.dep += (double)pr.local;
         for (int k = 0; k < pr.n; ++k) {
             int st = pr.type[k];
             R sT = pr.T[k];
             if (sT < R(p.cut[st])) {
-                deposit(p, t.ev, t.vol, (double)sT + rest_energy(st));
+                fx.dep += (double)sT + rest_energy(st);
                 continue;
             }
             sec_type[nsec] = st;
@@ -278,7 +297,7 @@ __device__ __forceinline__ void step_track(const Params<R>& p, TrackReg<R>& t, S
             if (!pr.parent_alive) {
                 alive = false;
             } else if (t.T < R(p.cut[t.type])) {
-                deposit(p, t.ev, t.vol, (double)t.T + rest_energy(t.type));
+                fx.dep += (double)t.T + rest_energy(t.type);
                 alive = false;
             }
         }
@@ -287,7 +306,7 @@ __device__ __forceinline__ void step_track(const Params<R>& p, TrackReg<R>& t, S
     const uint32_t parent_step = t.step;
     t.step += 1;
     if (alive && (int)t.step >= p.max_steps) {
-        atomicAdd(&p.ledger[3 * (size_t)t.ev + 1], (double)t.T + rest_energy(t.type));
+        fx.kill = (double)t.T + rest_energy(t.type);
         alive = false;
     }
     if (alive) {
@@ -300,7 +319,7 @@ __device__ __forceinline__ void step_track(const Params<R>& p, TrackReg<R>& t, S
         o.step[0] = t.step;
         o.n = 1;
     } else {
-        finish_track(p, t.ev, t.step);
+        fx.finished = true;
     }
     for (int k = 0; k < nsec; ++k) {
         int j = o.n;
@@ -313,7 +332,17 @@ __device__ __forceinline__ void step_track(const Params<R>& p, TrackReg<R>& t, S
         o.step[j] = 0;
         o.n = j + 1;
     }
-    update_live(p, t.ev, nsec - (alive ? 0 : 1));
+    fx.live_delta = nsec - (alive ? 0 : 1);
+}
+
+template <typename R>
+__device__ __forceinline__ void apply_effects(const Params<R>& p, uint32_t ev, uint32_t steps, const Effects& fx)
+{
+    deposit_now(p, ev, fx.vol, fx.dep);
+    if (fx.esc != 0.0) atomicAdd(&p.ledger[3 * (size_t)ev + 0], fx.esc);
+    if (fx.kill != 0.0) atomicAdd(&p.ledger[3 * (size_t)ev + 1], fx.kill);
+    if (fx.finished) finish_track(p, ev, steps);
+    update_live(p, ev, fx.live_delta);
 }
 
 template <typename R>
@@ -352,9 +381,16 @@ __device__ __forceinline__ void store_track(const Tracks<R>& q, long long i, con
 }
 
 // One step-loop iteration over both particle queues of side `side`.
-// Counter slots: cin = this step's input counts (and chunk dispenser),
-// cout = output counts (zero on entry), cclr = slot cleared for the next
-// step (it held the previous step's input).
+// Counter slots: cin = this step's input counts, chunk dispenser and
+// growth-token tally; cout = output counts (zero on entry); cclr = slot
+// cleared for the next step (it held the previous step's input).
+//
+// Capacity: each input track owns one output slot (its survivor, or its
+// copy when it is deferred).  A step never makes more than two outputs, so
+// only a step with two outputs needs one of the Q - n spare slots: it takes
+// a growth token first, and without one the step is discarded and the track
+// is copied unchanged (its step counter, hence its random stream, is kept).
+// When 2n <= Q every step fits and no token is counted.
 template <typename R>
 __global__ void __launch_bounds__(256) k_step(Params<R> p, int side, int cin, int cout, int cclr)
 {
@@ -363,7 +399,7 @@ __global__ void __launch_bounds__(256) k_step(Params<R> p, int side, int cin, in
         p.cnt[cclr].n[0] = 0;
         p.cnt[cclr].n[1] = 0;
         p.cnt[cclr].work = 0;
-        p.cnt[cclr].deferred = 0;
+        p.cnt[cclr].used = 0;
     }
     const Tracks<R> qi = p.q[side];
     const Tracks<R> qo = p.q[side ^ 1];
@@ -371,14 +407,13 @@ __global__ void __launch_bounds__(256) k_step(Params<R> p, int side, int cin, in
     const int nC = p.cnt[cin].n[1];
     const long long Q = p.Q;
     const long long ntot = (long long)nG + nC;
-    long long pmax = (Q - ntot) / 2;
-    if (pmax < 0) pmax = 0;
-    const long long pC = nC < pmax ? nC : pmax;
-    const long long pG = nG < pmax - pC ? nG : pmax - pC;
+    const long long spare = Q - ntot;
+    const bool unlimited = 2 * ntot <= Q;
     const int bs = blockDim.x;
     const int chunksG = (nG + bs - 1) / bs;
     const int chunksC = (nC + bs - 1) / bs;
     const int lane = threadIdx.x & 31;
+    const unsigned lanes_below = (1u << lane) - 1u;
 
     for (;;) {
         if (threadIdx.x == 0) s_chunk = atomicAdd(&p.cnt[cin].work, 1);
@@ -386,39 +421,61 @@ __global__ void __launch_bounds__(256) k_step(Params<R> p, int side, int cin, in
         const int chunk = s_chunk;
         __syncthreads();
         if (chunk >= chunksG + chunksC) break;
-        bool photon_chunk = chunk < chunksG;
-        long long i = photon_chunk ? (long long)chunk * bs + threadIdx.x
-                                   : (long long)(chunk - chunksG) * bs + threadIdx.x;
+        const bool photon_chunk = chunk < chunksG;
+        const long long i = photon_chunk ? (long long)chunk * bs + threadIdx.x
+                                         : (long long)(chunk - chunksG) * bs + threadIdx.x;
         const long long n_here = photon_chunk ? nG : nC;
         const bool active = i < n_here;
-        const bool stepping = active && i < (photon_chunk ? pG : pC);
         const long long src = photon_chunk ? i : Q - nC + i;
-        if (threadIdx.x == 0) {
-            long long lim = photon_chunk ? pG : pC;
-            long long c0 = photon_chunk ? (long long)chunk * bs : (long long)(chunk - chunksG) * bs;
-            long long c1 = c0 + bs < lim ? c0 + bs : lim;
-            long long e1 = c0 + bs < n_here ? c0 + bs : n_here;
-            if (c1 > c0) atomicAdd(&p.total_steps[0], (unsigned long long)(c1 - c0));
-            long long nd = e1 - (c1 > c0 ? c1 : c0);
-            if (nd > 0) atomicAdd(&p.total_steps[1], (unsigned long long)nd);
-        }
 
         TrackReg<R> t;
         StepOut<R> o;
+        Effects fx;
         o.n = 0;
+        bool stepped = false;
         if (active) {
             load_track(qi, src, t);
-            if (stepping) {
-                step_track(p, t, o);
-            } else {
-                o.n = 1;
-                o.type[0] = t.type;
-                o.T[0] = t.T;
-                o.u[0][0] = t.u[0];
-                o.u[0][1] = t.u[1];
-                o.u[0][2] = t.u[2];
-                o.uid[0] = t.uid;
-                o.step[0] = t.step;
+            step_track(p, t, o, fx);
+            stepped = true;
+        }
+        if (!unlimited) {
+            const bool need = stepped && o.n == 2;
+            const unsigned m = __ballot_sync(0xFFFFFFFFu, need);
+            if (m) {
+                const int k = __popc(m);
+                const int leader = __ffs(m) - 1;
+                int got = 0;
+                if (lane == leader) {
+                    int old = atomicAdd(&p.cnt[cin].used, k);
+                    long long avail = spare - old;
+                    got = avail <= 0 ? 0 : (avail >= k ? k : (int)avail);
+                    if (got < k) atomicSub(&p.cnt[cin].used, k - got);
+                }
+                got = __shfl_sync(0xFFFFFFFFu, got, leader);
+                if (need && __popc(m & lanes_below) >= got) {
+                    // no room for the second output: discard the step
+                    load_track(qi, src, t);
+                    stepped = false;
+                }
+            }
+        }
+        if (active && !stepped) {
+            o.n = 1;
+            o.type[0] = t.type;
+            o.T[0] = t.T;
+            o.u[0][0] = t.u[0];
+            o.u[0][1] = t.u[1];
+            o.u[0][2] = t.u[2];
+            o.uid[0] = t.uid;
+            o.step[0] = t.step;
+        }
+        if (stepped) apply_effects(p, t.ev, t.step, fx);
+        {
+            const unsigned ms = __ballot_sync(0xFFFFFFFFu, stepped);
+            const unsigned md = __ballot_sync(0xFFFFFFFFu, active && !stepped);
+            if (lane == 0) {
+                if (ms) atomicAdd(&p.total_steps[0], (unsigned long long)__popc(ms));
+                if (md) atomicAdd(&p.total_steps[1], (unsigned long long)__popc(md));
             }
         }
         // warp-aggregated reservation: counts packed as g | c << 16
@@ -429,15 +486,15 @@ __global__ void __launch_bounds__(256) k_step(Params<R> p, int side, int cin, in
             else
                 ++nc;
         }
-        int v = ng | (nc << 16);
+        const int v = ng | (nc << 16);
         int incl = v;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             int y = __shfl_up_sync(0xFFFFFFFFu, incl, off);
             if (lane >= off) incl += y;
         }
-        int excl = incl - v;
-        int tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        const int excl = incl - v;
+        const int tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
         int baseG = 0, baseC = 0;
         if (lane == 31) {
             int tg = tot & 0xFFFF, tc = tot >> 16;
@@ -509,7 +566,7 @@ __global__ void k_admit(Params<R> p, int side, int cs, int n, const int32_t* ev,
             if (vol == kVolOut) {
                 atomicAdd(&p.ledger[3 * (size_t)t.ev + 0], E);
             } else if (T[i] < p.cut[t.type]) {
-                deposit(p, t.ev, vol, E);
+                deposit_now(p, t.ev, vol, E);
             } else {
                 keep = true;
                 atomicAdd(&p.live[t.ev], 1);
@@ -557,6 +614,7 @@ __global__ void k_set_tracks(Params<R> p, int side, int cs, int n, const double*
         atomicOr(p.status, kStatusQueueOverflow);
         return;
     }
+    atomicAdd(&p.live[slot[i]], 1);
     store_track(p.q[side], dst, x, u, R(r[1]), uid[i], (uint32_t)slot[i], (uint32_t)r[9], type, (int)r[8]);
 }
 

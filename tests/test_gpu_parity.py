@@ -60,17 +60,23 @@ def compare_events(summ, osumm, hist=None, ohist=None, frac=0.999):
 
 
 def test_tables_match_oracle(emt, oracle_mod):
+    """Every table node within 1e-13 relative at and above the cuts (the
+    energies tracks are transported at).  Below, the Klein-Nishina closed
+    form cancels like 1/kappa^2 (kappa = k/me ~ 2e-3 at 1 keV), so last-bit
+    differences of log() between libm and CUDA grow to ~1e-16/kappa^2."""
     for s in (W.calo_setup(), W.slab_setup()):
         ctx = emt.context_for(s, slot_capacity=1 << 12, max_events=4)
         o = oracle_of(oracle_mod, s)
         g = ctx.get_table(0, 0, 5)
         assert np.allclose(g, o.grid(), rtol=1e-15, atol=0)
+        kappa = g / 0.51099895
+        tol = np.where(g >= 0.5 * s.physics[0], 1e-13, np.maximum(1e-13, 1e-15 / kappa ** 2))
         for m in range(len(s.materials)):
             for p, qs in ((0, (0, 1, 2)), (1, (0, 1, 3, 4)), (2, (0, 1, 2, 3, 4))):
                 for q in qs:
                     a, b = ctx.get_table(m, p, q), o.table(m, p, q)
                     scale = np.maximum(np.abs(b), 1e-300)
-                    assert np.all(np.abs(a - b) / scale <= 1e-13), (m, p, q)
+                    assert np.all(np.abs(a - b) / scale <= tol), (m, p, q)
         ctx.close()
 
 
@@ -130,13 +136,14 @@ def test_single_step_parity(emt, oracle_mod, setup):
     # outputs of each input track: survivor and secondaries above the cut
     missing = set(want) - set(got)
     extra = set(got) - set(want)
-    assert len(missing) + len(extra) <= n * 1e-3, (len(missing), len(extra))
-    bad = 0
+    assert len(missing) + len(extra) <= n * 1e-3, (
+        len(missing), len(extra), [want[u] for u in list(missing)[:3]], [got[u] for u in list(extra)[:3]])
+    bad = []
     for u in set(want) & set(got):
         a, b = got[u], want[u]
         if a[0] != b[0] or a[8] != b[8] or a[9] != b[9] or not np.allclose(a[1:8], b[1:8], rtol=1e-11, atol=1e-11):
-            bad += 1
-    assert bad <= n * 1e-3, bad
+            bad.append((a, b))
+    assert len(bad) <= n * 1e-3, (len(bad), bad[:3])
     # per-event deposits, escapes and kills of the single step
     ctx.debug_set_tracks(np.zeros((0, 10)), np.zeros(0, np.uint64), np.zeros(0, np.int32))
     hist, summ, ids = ctx.read_all()

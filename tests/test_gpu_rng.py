@@ -20,7 +20,7 @@ def curand_lib():
     subprocess.check_call(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-shared",
                            "-Xcompiler", "-fPIC", "-o", so, src])
     L = ctypes.CDLL(so)
-    L.curand_philox.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_void_p]
+    L.curand_philox.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
     return L
 
 
