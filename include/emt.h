@@ -224,6 +224,49 @@ emt_status emt_debug_set_tracks(emt_ctx* ctx, int32_t n, const double* rec, cons
 emt_status emt_debug_get_tracks(emt_ctx* ctx, int32_t cap, double* rec, uint64_t* uid, int32_t* event_slot,
                                 int32_t* n_out);
 
+/* ---------------------------------------------------------------------
+ * Allocation-free transport.  The paper has no counterpart to this call.
+ *
+ * For callers that must not allocate device memory: code running inside a
+ * framework whose caching allocator already owns the GPU's memory, a host
+ * plugin whose sandbox forbids new device allocations, or a latency-bound
+ * serving loop that cannot afford the device-wide synchronisation a
+ * cudaMalloc/cudaFree may cause.  This one call transports a small batch
+ * of events from start to finish (FP64, plain step loop) using only a
+ * fixed device array compiled into the library (64 MiB, held by every GPU
+ * that loads the library until the process exits).  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *
+ * Limits (larger inputs return EMT_ERR_CAPACITY, nothing is run):
+ * n_events <= EMT_STATIC_MAX_EVENTS, prim->n <= EMT_STATIC_MAX_PRIMARIES,
+ * world->n_bins <= EMT_STATIC_MAX_BINS, and the tracks in flight at any
+ * step <= EMT_STATIC_MAX_TRACKS (a step that would exceed it is deferred;
+ * if no track can advance the call returns EMT_ERR_CAPACITY).
+ *
+ * Arguments: device ordinal; seed; host arrays mats[n_mat], phys,
+ * layers[n_layers], world, event_ids[n_events] (as emt_load_materials,
+ * emt_load_geometry and emt_submit); prim: device arrays grouped by event
+ * as in emt_submit; hist[n_events][n_bins] and summary[n_events][6]:
+ * caller-owned device buffers written in event order; cuda_stream: the
+ * stream to run on (NULL: the legacy default stream).  Returns when the
+ * results are complete.
+ *
+ * The first call on a device looks up the device address of the fixed
+ * array (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Every call reuses the same array and clears what must start
+ * at zero, so calls that overlap on the GPU (from two threads or on two
+ * streams) race with each other: serialize them.
+ * --------------------------------------------------------------------- */
+#define EMT_STATIC_MAX_EVENTS 256
+#define EMT_STATIC_MAX_PRIMARIES 65536
+#define EMT_STATIC_MAX_BINS 128
+#define EMT_STATIC_MAX_TRACKS (1 << 18)
+
+emt_status emt_transport_static(int32_t device, uint32_t seed, const emt_material* mats, int32_t n_mat,
+                                const emt_physics* phys, const emt_layer* layers, int32_t n_layers,
+                                const emt_world* world, int32_t n_events, const uint64_t* event_ids,
+                                const emt_primaries* prim, double* hist, double* summary, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

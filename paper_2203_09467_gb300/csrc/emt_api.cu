@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <unordered_map>
@@ -1019,3 +1020,245 @@ emt_status emt_debug_get_tracks(emt_ctx* c, int32_t cap, double* rec, uint64_t* 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free entry point.  The paper has no counterpart: this exists
+// for callers that must not allocate device memory (see include/emt.h).
+// All device scratch (track buffers, counters, tables, geometry, scores)
+// lives in one file-scope device array of kStaticPoolBytes.  Host code must
+// not use the array's name as a device address: the address comes from
+// cudaGetSymbolAddress, once per device, with that device current.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticPoolBytes = (size_t)64 << 20;
+__device__ __align__(256) unsigned char g_static_pool[kStaticPoolBytes];
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mutex;
+void* g_static_ptr[kStaticMaxDevices] = {};
+
+emt_options static_options(int32_t device, uint32_t seed)
+{
+    emt_options o;
+    emt_default_options(&o);
+    o.device = device;
+    o.precision = EMT_PRECISION_FP64;
+    o.slot_capacity = EMT_STATIC_MAX_TRACKS;
+    o.max_events = EMT_STATIC_MAX_EVENTS;
+    o.max_bins = EMT_STATIC_MAX_BINS;
+    o.seed = seed;
+    return o;
+}
+
+}  // namespace
+
+extern "C" emt_status emt_transport_static(int32_t device, uint32_t seed, const emt_material* mats, int32_t n_mat,
+                                           const emt_physics* ph, const emt_layer* layers, int32_t n_layers,
+                                           const emt_world* w, int32_t n_events, const uint64_t* event_ids,
+                                           const emt_primaries* prim, double* hist, double* summary,
+                                           void* cuda_stream)
+{
+    // ---- arguments (sizes beyond the static limits are rejected)
+    if (!mats || !ph || !layers || !w || !event_ids || !prim || !summary) return EMT_ERR_INVALID_ARG;
+    if (n_events < 1 || n_events > EMT_STATIC_MAX_EVENTS) return EMT_ERR_CAPACITY;
+    if (prim->n < 0 || prim->n > EMT_STATIC_MAX_PRIMARIES) return EMT_ERR_CAPACITY;
+    if (w->n_bins < 1 || w->n_bins > EMT_STATIC_MAX_BINS) return EMT_ERR_CAPACITY;
+    if (n_mat < 1 || n_mat > kMaxMat || n_layers < 1 || n_layers > kMaxLayers) return EMT_ERR_CAPACITY;
+    if (prim->n > 0 && (!prim->event || !prim->type || !prim->T_MeV || !prim->pos_cm || !prim->dir))
+        return EMT_ERR_INVALID_ARG;
+    if (w->n_bins > 0 && !hist) return EMT_ERR_INVALID_ARG;
+    if (!(ph->grid_lo_MeV > 0.0) || !(ph->grid_hi_MeV > ph->grid_lo_MeV) || ph->bins_per_decade < 1)
+        return EMT_ERR_INVALID_ARG;
+    const int n_grid = (int)std::floor(ph->bins_per_decade * std::log10(ph->grid_hi_MeV / ph->grid_lo_MeV) + 0.5) + 1;
+    if (n_grid < 2 || n_grid > kMaxGrid) return EMT_ERR_INVALID_ARG;
+    for (int k = 0; k < 3; ++k)
+        if (!(ph->cut_MeV[k] > 0.0)) return EMT_ERR_INVALID_ARG;
+    if (!(ph->step_frac > 0.0) || !(ph->final_range_cm > 0.0) || w->max_steps < 1) return EMT_ERR_INVALID_ARG;
+    if (!(w->half_x_cm > 0.0) || !(w->half_y_cm > 0.0)) return EMT_ERR_INVALID_ARG;
+    for (int e = 0; e < n_events; ++e)
+        for (int f = e + 1; f < n_events; ++f)
+            if (event_ids[e] == event_ids[f]) return EMT_ERR_INVALID_ARG;
+    if (device < 0 || device >= kStaticMaxDevices) return EMT_ERR_INVALID_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return EMT_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+
+    // ---- device address of the static array (set-up, once per device)
+    char* pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_static_mutex);
+        if (!g_static_ptr[device]) {
+            void* ptr = nullptr;
+            if (cudaGetSymbolAddress(&ptr, g_static_pool) != cudaSuccess || !ptr) return EMT_ERR_CUDA;
+            g_static_ptr[device] = ptr;
+        }
+        pool = (char*)g_static_ptr[device];
+    }
+    const emt_options opt = static_options(device, seed);
+    const Plan pl = make_plan(opt);
+    if (pl.total > kStaticPoolBytes) return EMT_ERR_CAPACITY;
+
+    // ---- parameters pointing into the static array
+    emt_ctx view;  // holds no resources: only the pool layout for fill_common
+    view.opt = opt;
+    view.plan = pl;
+    view.pool = pool;
+    Params<double> p;
+    std::memset(&p, 0, sizeof p);
+    fill_common(&view, p);
+
+    // ---- zero what must start at zero (the array keeps the last call's data)
+    if (cudaMemsetAsync(pool + pl.cnt, 0, pl.hist - pl.cnt, st) != cudaSuccess) return EMT_ERR_CUDA;
+    if (cudaMemsetAsync(pool + pl.live, 0, pl.grid - pl.live, st) != cudaSuccess) return EMT_ERR_CUDA;
+
+    // ---- materials and tables
+    MaterialDev md[kMaxMat];
+    double bk[kMaxMat];
+    int vac[kMaxMat];
+    for (int i = 0; i < n_mat; ++i) {
+        const emt_material& m = mats[i];
+        const bool vacuum = !(m.rho_g_cm3 > 0.0);
+        if (!vacuum && (!(m.Z >= 1.0) || !(m.A_g_mol > 0.0) || !(m.I_eV > 0.0) || !(m.bk_MeV >= 0.0)))
+            return EMT_ERR_INVALID_ARG;
+        md[i] = {m.Z, m.A_g_mol, vacuum ? 0.0 : m.rho_g_cm3, m.I_eV, m.bk_MeV};
+        bk[i] = m.bk_MeV;
+        vac[i] = vacuum ? 1 : 0;
+    }
+    if (cudaMemcpyAsync(pool + pl.mats, md, sizeof(MaterialDev) * n_mat, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(pool + pl.bk, bk, sizeof(double) * n_mat, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(pool + pl.vacuum, vac, sizeof(int) * n_mat, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return EMT_ERR_CUDA;
+    TableBuild b;
+    b.mats = reinterpret_cast<const MaterialDev*>(pool + pl.mats);
+    b.n_mat = n_mat;
+    b.n_grid = n_grid;
+    b.bpd = ph->bins_per_decade;
+    b.e_lo = ph->grid_lo_MeV;
+    for (int k = 0; k < 3; ++k) b.cut[k] = ph->cut_MeV[k];
+    b.mask = ph->process_mask;
+    b.grid = reinterpret_cast<double*>(pool + pl.grid);
+    b.tab = reinterpret_cast<double*>(pool + pl.tab);
+    b.dedx = reinterpret_cast<double*>(pool + pl.dedx);
+    b.tabf = nullptr;
+    b.gridf = nullptr;
+    if (build_tables(b, reinterpret_cast<double*>(pool + pl.scratch), st) != cudaSuccess) return EMT_ERR_CUDA;
+    for (int k = 0; k < 3; ++k) p.cut[k] = ph->cut_MeV[k];
+    p.grid = b.grid;
+    p.tab = b.tab;
+    p.n_grid = n_grid;
+    p.bpd = ph->bins_per_decade;
+    p.log10_lo = (float)std::log10(ph->grid_lo_MeV);
+    p.step_frac = ph->step_frac;
+    p.final_range = ph->final_range_cm;
+
+    // ---- geometry
+    double zb[kMaxLayers + 1];
+    int lm[kMaxLayers], lb[kMaxLayers];
+    zb[0] = w->z0_cm;
+    for (int i = 0; i < n_layers; ++i) {
+        if (!(layers[i].thickness_cm > 0.0) || layers[i].material < -1 || layers[i].material >= n_mat)
+            return EMT_ERR_INVALID_ARG;
+        zb[i + 1] = zb[i] + layers[i].thickness_cm;
+        lm[i] = layers[i].material;
+        lb[i] = layers[i].score_bin;
+    }
+    const double glo[3] = {-w->half_x_cm, -w->half_y_cm, zb[0]};
+    const double ghi[3] = {w->half_x_cm, w->half_y_cm, zb[n_layers]};
+    for (int a = 0; a < 3; ++a)
+        if (!(w->lo_cm[a] <= glo[a]) || !(w->hi_cm[a] >= ghi[a])) return EMT_ERR_INVALID_ARG;
+    const double bmag =
+        std::sqrt(w->B_tesla[0] * w->B_tesla[0] + w->B_tesla[1] * w->B_tesla[1] + w->B_tesla[2] * w->B_tesla[2]);
+    if (bmag > 0.0 && (!(w->rk_delta_cm > 0.0) || !(w->max_field_step_cm > 0.0))) return EMT_ERR_INVALID_ARG;
+    if (cudaMemcpyAsync(pool + pl.zb, zb, sizeof(double) * (n_layers + 1), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(pool + pl.lmat, lm, sizeof(int) * n_layers, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(pool + pl.lbin, lb, sizeof(int) * n_layers, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return EMT_ERR_CUDA;
+    p.n_layers = n_layers;
+    p.hx = w->half_x_cm;
+    p.hy = w->half_y_cm;
+    for (int a = 0; a < 3; ++a) {
+        p.wlo[a] = w->lo_cm[a];
+        p.whi[a] = w->hi_cm[a];
+        p.B[a] = w->B_tesla[a];
+    }
+    p.bmag = bmag;
+    p.rk_delta = w->rk_delta_cm;
+    p.max_field_step = w->max_field_step_cm;
+    p.has_field = bmag > 0.0 ? 1 : 0;
+    p.max_steps = w->max_steps;
+    p.n_bins = w->n_bins;
+
+    // ---- events: slots 0..n_events-1 in order; primaries read in place
+    uint32_t slots[EMT_STATIC_MAX_EVENTS];
+    for (int e = 0; e < n_events; ++e) slots[e] = (uint32_t)e;
+    if (cudaMemcpyAsync(pool + pl.st_slot, slots, 4 * (size_t)n_events, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(pool + pl.st_ids, event_ids, 8 * (size_t)n_events, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(pool + pl.st_runs, 0, 4 * (size_t)n_events, st) != cudaSuccess)
+        return EMT_ERR_CUDA;
+    const int n = prim->n;
+    int* status = reinterpret_cast<int*>(pool + pl.status);
+    uint32_t* st_slot = reinterpret_cast<uint32_t*>(pool + pl.st_slot);
+    if (n > 0) {
+        k_runs<<<(n + 255) / 256, 256, 0, st>>>(prim->event, n, n_events, reinterpret_cast<uint32_t*>(pool + pl.st_start),
+                                                reinterpret_cast<uint32_t*>(pool + pl.st_runs), status);
+        k_uids<<<(n + 255) / 256, 256, 0, st>>>(prim->event, n, reinterpret_cast<uint32_t*>(pool + pl.st_start),
+                                                reinterpret_cast<uint32_t*>(pool + pl.st_runs),
+                                                reinterpret_cast<uint32_t*>(pool + pl.st_uid), status);
+    }
+    int h_status = 0;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return EMT_ERR_CUDA;
+    if (h_status != 0) return EMT_ERR_INVALID_ARG;
+    k_reset_slots<<<(n_events + 127) / 128, 128, 0, st>>>(st_slot, n_events, p.hist, pl.hstride, p.ledger, p.counts,
+                                                          p.live, reinterpret_cast<uint64_t*>(pool + pl.event_id),
+                                                          reinterpret_cast<const uint64_t*>(pool + pl.st_ids));
+    if (Launch<double>::admit(p, 0, 0, n, prim->event, prim->type, prim->T_MeV, prim->pos_cm, prim->dir, st_slot,
+                              reinterpret_cast<const uint32_t*>(pool + pl.st_uid), st) != cudaSuccess)
+        return EMT_ERR_CUDA;
+    k_release_tokens<<<(n_events + 127) / 128, 128, 0, st>>>(st_slot, n_events, p.live, p.done_ring, p.done_head,
+                                                             pl.max_events);
+    if (cudaGetLastError() != cudaSuccess) return EMT_ERR_CUDA;
+
+    // ---- step loop (host-driven; one counter read per step)
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    const int block = 128;
+    const int resident = std::max(1, sms * Launch<double>::max_blocks_per_sm(block));
+    Counters h_cnt;
+    if (cudaMemcpyAsync(&h_cnt, pool + pl.cnt, sizeof h_cnt, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return EMT_ERR_CUDA;
+    int64_t live_g = h_cnt.n[0], live_c = h_cnt.n[1];
+    unsigned long long steps[2] = {0, 0}, last_steps = 0;
+    for (int64_t it = 0; live_g + live_c > 0; ++it) {
+        const int side = (int)(it & 1), cin = (int)(it % 3), cout = (int)((it + 1) % 3), cclr = (int)((it + 2) % 3);
+        const int64_t chunks = (live_g + block - 1) / block + (live_c + block - 1) / block;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(chunks, resident));
+        if (Launch<double>::step(p, side, cin, cout, cclr, grid, block, st) != cudaSuccess) return EMT_ERR_CUDA;
+        if (cudaMemcpyAsync(&h_cnt, pool + pl.cnt + sizeof(Counters) * ((it + 1) % 3), sizeof h_cnt,
+                            cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return EMT_ERR_CUDA;
+        const bool same = live_g == h_cnt.n[0] && live_c == h_cnt.n[1];
+        live_g = h_cnt.n[0];
+        live_c = h_cnt.n[1];
+        if (same && live_g + live_c > 0) {
+            if (cudaMemcpyAsync(steps, pool + pl.total_steps, sizeof steps, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                return EMT_ERR_CUDA;
+            if (steps[0] == last_steps) return EMT_ERR_CAPACITY;
+            last_steps = steps[0];
+        }
+    }
+
+    // ---- results straight into the caller's device buffers
+    k_gather<<<(n_events + 127) / 128, 128, 0, st>>>(st_slot, n_events, p.hist, pl.hstride, w->n_bins, p.ledger,
+                                                     p.counts, hist, summary);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return EMT_ERR_CUDA;
+    return (h_status & (kStatusQueueOverflow | kStatusBadTrack)) ? EMT_ERR_CUDA : EMT_OK;
+}

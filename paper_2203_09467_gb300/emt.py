@@ -95,6 +95,11 @@ _SIGS = {
                                               ctypes.c_void_p]),
     "emt_debug_get_tracks": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]),
+    "emt_transport_static": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_uint32, ctypes.POINTER(Material),
+                                              ctypes.c_int32, ctypes.POINTER(Physics), ctypes.POINTER(Layer),
+                                              ctypes.c_int32, ctypes.POINTER(World), ctypes.c_int32,
+                                              ctypes.c_void_p, ctypes.POINTER(Primaries), ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 
