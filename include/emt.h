@@ -80,7 +80,7 @@ typedef struct emt_options {
     int64_t slot_capacity; /* tracks in flight per step (each of two ping-pong buffers) */
     int32_t max_events;    /* events that can be in flight (score slots) */
     int32_t max_bins;      /* histogram width capacity (>= emt_world.n_bins) */
-    int32_t block_size;    /* threads per block of the step kernel; 0 = default */
+    int32_t block_size;    /* threads per block of the step kernel: 128 or 256; 0 = 256 */
     int32_t loop_mode;     /* EMT_LOOP_* */
     int32_t graph_steps;   /* steps per graph launch (EMT_LOOP_GRAPH); multiple of 6 */
     uint32_t seed;         /* random stream seed */

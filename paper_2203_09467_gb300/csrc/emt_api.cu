@@ -106,8 +106,8 @@ bool valid_options(const emt_options& o, std::string& why)
     if (o.slot_capacity < 64 || o.slot_capacity > (int64_t)1 << 30) return why = "slot_capacity out of [64, 2^30]", false;
     if (o.max_events < 1 || o.max_events > (1 << 24)) return why = "max_events out of [1, 2^24]", false;
     if (o.max_bins < 1 || o.max_bins > 65536) return why = "max_bins out of [1, 65536]", false;
-    if (o.block_size != 0 && (o.block_size % 32 != 0 || o.block_size < 32 || o.block_size > 256))
-        return why = "block_size must be a multiple of 32 in [32, 256]", false;
+    if (o.block_size != 0 && o.block_size != 128 && o.block_size != 256)
+        return why = "block_size must be 0 (default), 128 or 256", false;
     if (o.loop_mode != EMT_LOOP_PLAIN && o.loop_mode != EMT_LOOP_GRAPH) return why = "loop_mode", false;
     if (o.loop_mode == EMT_LOOP_GRAPH && (o.graph_steps <= 0 || o.graph_steps % 6 != 0))
         return why = "graph_steps must be a positive multiple of 6", false;
@@ -551,7 +551,7 @@ emt_status emt_create(const emt_options* o, emt_ctx** out)
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(EMT_ERR_CUDA);
     fill_common(c, c->pd);
     fill_common(c, c->pf);
-    c->block = o->block_size ? o->block_size : 128;
+    c->block = o->block_size ? o->block_size : 256;
     int dev_sms = 0;
     cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, o->device);
     int per_sm = c->mixed() ? Launch<float>::max_blocks_per_sm(c->block) : Launch<double>::max_blocks_per_sm(c->block);
@@ -1224,7 +1224,7 @@ extern "C" emt_status emt_transport_static(int32_t device, uint32_t seed, const 
     // ---- step loop (host-driven; one counter read per step)
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    const int block = 128;
+    const int block = 256;
     const int resident = std::max(1, sms * Launch<double>::max_blocks_per_sm(block));
     Counters h_cnt;
     if (cudaMemcpyAsync(&h_cnt, pool + pl.cnt, sizeof h_cnt, cudaMemcpyDeviceToHost, st) != cudaSuccess ||

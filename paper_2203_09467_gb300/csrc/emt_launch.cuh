@@ -11,7 +11,12 @@ template <typename R>
 cudaError_t Launch<R>::step(const Params<R>& p, int side, int cin, int cout, int cclr, int grid, int block,
                             cudaStream_t st)
 {
-    k_step<R><<<grid, block, 0, st>>>(p, side, cin, cout, cclr);
+    if (block == 128)
+        k_step<R, 128><<<grid, 128, 0, st>>>(p, side, cin, cout, cclr);
+    else if (block == 256)
+        k_step<R, 256><<<grid, 256, 0, st>>>(p, side, cin, cout, cclr);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
@@ -48,7 +53,9 @@ template <typename R>
 int Launch<R>::max_blocks_per_sm(int block)
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<R>, block, 0) != cudaSuccess) return 1;
+    cudaError_t e = block == 128 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<R, 128>, 128, 0)
+                                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<R, 256>, 256, 0);
+    if (e != cudaSuccess) return 1;
     return n > 0 ? n : 1;
 }
 

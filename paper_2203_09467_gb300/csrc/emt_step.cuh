@@ -13,6 +13,14 @@
 //  * Work is handed out in chunks of blockDim.x tracks of one particle type
 //    by an atomic dispenser, so every warp runs the photon or the charged
 //    code path only, and blocks stay busy until the step is drained.
+//  * Within a chunk the step runs in two phases.  Phase A (every lane, its
+//    own track): cross sections, step limits, propagation, continuous loss,
+//    boundary and process selection.  Tracks that interact are counting-
+//    sorted by model into shared memory; phase B runs the samplers over the
+//    sorted records, so a warp executes one model (or two, at a group
+//    boundary) instead of every model its lanes happened to select.  This
+//    is the paper's one-kernel-per-model idea (Sec. 3.2) done inside one
+//    launch, without a round trip through device memory.
 //  * Output slots are reserved once per warp: a shuffle prefix sum over the
 //    lanes' photon and charged output counts and one atomicAdd per type.
 //  * Capacity: a step whose outputs do not fit is discarded and the track
@@ -38,16 +46,16 @@ struct TrackReg {
     int vol;
 };
 
-// outputs of one input track: survivor first, then secondaries; all share
-// the post-step position, event and volume
+// outputs sharing one position, event and volume: survivor first, then
+// secondaries
 template <typename R>
 struct StepOut {
     int n;
-    int type[3];
-    R T[3];
-    R u[3][3];
-    uint64_t uid[3];
-    uint32_t step[3];
+    int type[2];
+    R T[2];
+    R u[2][3];
+    uint64_t uid[2];
+    uint32_t step[2];
 };
 
 // Side effects of one step, staged in registers and applied only once the
@@ -61,6 +69,19 @@ struct Effects {
     int vol;      // volume of the deposits
     bool finished;
     int live_delta;
+};
+
+// models, in the order of the cumulative selection per particle type
+enum Model : int {
+    kPhoto = 0,
+    kCompton = 1,
+    kPair = 2,
+    kMoller = 3,
+    kBhabha = 4,
+    kBrems = 5,
+    kAnnih = 6,
+    kNumModels = 7,
+    kNoInteraction = -1
 };
 
 template <typename R>
@@ -98,20 +119,31 @@ __device__ __forceinline__ void update_live(const Params<R>& p, uint32_t ev, int
     }
 }
 
-// One step of one track; the order is
+template <typename R>
+__device__ __forceinline__ void apply_effects(const Params<R>& p, uint32_t ev, uint32_t steps, const Effects& fx)
+{
+    deposit_now(p, ev, fx.vol, fx.dep);
+    if (fx.esc != 0.0) atomicAdd(&p.ledger[3 * (size_t)ev + 0], fx.esc);
+    if (fx.kill != 0.0) atomicAdd(&p.ledger[3 * (size_t)ev + 1], fx.kill);
+    if (fx.finished) finish_track(p, ev, steps);
+    update_live(p, ev, fx.live_delta);
+}
+
+// Phase A of one step of one track, in the order
 //  1 cross sections at the pre-step energy   2 s_int = -ln(u0)/Sigma_tot
 //  3 e+-: s_max = max(f R, min(R, r_final))  4 s_phys = min
 //  5 propagate to min(s_phys, boundary), ties to the boundary
 //  6 e+-: T' = R^-1(R(T) - s), deposit T - T'
 //  7 e+- below the cut: deposit T' (+2 me for e+), track ends
 //  8 boundary: logical volume update; leaving the world tallies escape
-//  9 interaction: process by u1 Sigma_tot against the cumulative pre-step
-//    Sigma's, sampled with the post-loss energy
-// 10 step += 1; at max_steps the track is killed
+//  9 interaction: the model by u1 Sigma_tot against the cumulative pre-step
+//    Sigma's; a model whose channel is closed at the post-loss energy makes
+//    a null interaction.
+// Returns the model to sample in phase B, or kNoInteraction.  `alive`
+// reports whether the track survives phase A.
 template <typename R>
-__device__ __forceinline__ void step_track(const Params<R>& p, TrackReg<R>& t, StepOut<R>& o, Effects& fx)
+__device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t, Effects& fx, bool& alive)
 {
-    o.n = 0;
     fx.dep = 0.0;
     fx.esc = 0.0;
     fx.kill = 0.0;
@@ -196,7 +228,7 @@ __device__ __forceinline__ void step_track(const Params<R>& p, TrackReg<R>& t, S
     }
     if (boundary) interact = false;
 
-    bool alive = true;
+    alive = true;
     // 6-7: continuous loss
     if (charged && matter) {
         R r = Rng - R(s);
@@ -209,11 +241,6 @@ __device__ __forceinline__ void step_track(const Params<R>& p, TrackReg<R>& t, S
             alive = false;
         }
     }
-    int nsec = 0;
-    int sec_type[2];
-    R sec_T[2];
-    R sec_u[2][3];
-    int sec_k[2];
     // 8: boundary
     if (alive && boundary) {
         t.vol = e.next;
@@ -221,94 +248,46 @@ __device__ __forceinline__ void step_track(const Params<R>& p, TrackReg<R>& t, S
             fx.esc = (double)t.T + rest_energy(t.type);
             alive = false;
         }
-    } else if (alive && interact) {
-        // 9: select and sample
-        dr.next = 1;
-        R xsel = draw<R>(dr) * sig_tot;
-        int proc = nproc - 1;
-        R c = R(0);
-        for (int i = 0; i < nproc; ++i) {
-            c += sig[i];
-            if (xsel < c) {
-                proc = i;
-                break;
-            }
-        }
-        dr.next = 2;
-        Products<R> pr;
-        pr.n = 0;
-        pr.local = R(0);
-        pr.parent_alive = true;
-        bool null_interaction = false;
-        const R T = t.T;
-        const R cut_e = R(p.cut[1]), kc = R(p.cut[0]);
-        if (t.type == 0) {
-            if (proc == 0) {
-                R bk = R(p.bk[mi]);
-                if (T > bk)
-                    sample_photo(T, bk, t.u, pr);
-                else
-                    null_interaction = true;
-            } else if (proc == 1) {
-                sample_compton(dr, T, t.u, pr, t.T);
-            } else {
-                if (T > R(2.0 * kMe))
-                    sample_pair(dr, T, t.u, pr);
-                else
-                    null_interaction = true;
-            }
-        } else if (proc == 0) {
-            if (t.type == 1) {
-                if (T > R(2) * cut_e)
-                    sample_moller(dr, T, cut_e, t.u, pr, t.T);
-                else
-                    null_interaction = true;
-            } else {
-                if (T > cut_e)
-                    sample_bhabha(dr, T, cut_e, t.u, pr, t.T);
-                else
-                    null_interaction = true;
-            }
-        } else if (proc == 1) {
-            if (T > kc)
-                sample_brems(dr, T, kc, t.u, pr, t.T);
-            else
-                null_interaction = true;
-        } else {
-            sample_annih(dr, T, t.u, pr);
-        }
-        if (pr.local != R(0)) fx.dep += (double)pr.local;
-        for (int k = 0; k < pr.n; ++k) {
-            int st = pr.type[k];
-            R sT = pr.T[k];
-            if (sT < R(p.cut[st])) {
-                fx.dep += (double)sT + rest_energy(st);
-                continue;
-            }
-            sec_type[nsec] = st;
-            sec_T[nsec] = sT;
-            sec_u[nsec][0] = pr.dir[k][0];
-            sec_u[nsec][1] = pr.dir[k][1];
-            sec_u[nsec][2] = pr.dir[k][2];
-            sec_k[nsec] = k;
-            ++nsec;
-        }
-        if (!null_interaction) {
-            if (!pr.parent_alive) {
-                alive = false;
-            } else if (t.T < R(p.cut[t.type])) {
-                fx.dep += (double)t.T + rest_energy(t.type);
-                alive = false;
-            }
+        return kNoInteraction;
+    }
+    if (!alive || !interact) return kNoInteraction;
+    // 9: model selection (draw 1) and closed channels
+    dr.next = 1;
+    R xsel = draw<R>(dr) * sig_tot;
+    int proc = nproc - 1;
+    R c = R(0);
+    for (int i = 0; i < nproc; ++i) {
+        c += sig[i];
+        if (xsel < c) {
+            proc = i;
+            break;
         }
     }
-    // 10
-    const uint32_t parent_step = t.step;
+    const R T = t.T;
+    if (t.type == 0) {
+        if (proc == 0) return T > R(p.bk[mi]) ? kPhoto : kNoInteraction;
+        if (proc == 1) return kCompton;
+        return T > R(2.0 * kMe) ? kPair : kNoInteraction;
+    }
+    if (proc == 0) {
+        if (t.type == 1) return T > R(2) * R(p.cut[1]) ? kMoller : kNoInteraction;
+        return T > R(p.cut[1]) ? kBhabha : kNoInteraction;
+    }
+    if (proc == 1) return T > R(p.cut[0]) ? kBrems : kNoInteraction;
+    return kAnnih;
+}
+
+// step 10 for a track that did not interact: count the step, apply the
+// step limit, and emit the survivor
+template <typename R>
+__device__ __forceinline__ void finish_step(const Params<R>& p, TrackReg<R>& t, bool alive, Effects& fx, StepOut<R>& o)
+{
     t.step += 1;
     if (alive && (int)t.step >= p.max_steps) {
         fx.kill = (double)t.T + rest_energy(t.type);
         alive = false;
     }
+    o.n = 0;
     if (alive) {
         o.type[0] = t.type;
         o.T[0] = t.T;
@@ -320,7 +299,65 @@ __device__ __forceinline__ void step_track(const Params<R>& p, TrackReg<R>& t, S
         o.n = 1;
     } else {
         fx.finished = true;
+        fx.live_delta = -1;
     }
+}
+
+// Phase B: sample model `m` for the post-loss state t (draws 2, 3, ... of
+// the step), then step 10.  Secondaries below their cut deposit on the spot.
+template <typename R>
+__device__ __forceinline__ void interaction_part(const Params<R>& p, TrackReg<R>& t, int m, Effects& fx,
+                                                 StepOut<R>& o)
+{
+    const uint64_t event_id = p.event_id[t.ev];
+    Draws dr;
+    dr.init(p.seed, event_id, t.uid, t.step);
+    dr.next = 2;
+    Products<R> pr;
+    pr.n = 0;
+    pr.local = R(0);
+    pr.parent_alive = true;
+    const R T = t.T;
+    const R cut_e = R(p.cut[1]), kc = R(p.cut[0]);
+    switch (m) {
+    case kPhoto: sample_photo(T, R(p.bk[p.lmat[t.vol]]), t.u, pr); break;
+    case kCompton: sample_compton(dr, T, t.u, pr, t.T); break;
+    case kPair: sample_pair(dr, T, t.u, pr); break;
+    case kMoller: sample_moller(dr, T, cut_e, t.u, pr, t.T); break;
+    case kBhabha: sample_bhabha(dr, T, cut_e, t.u, pr, t.T); break;
+    case kBrems: sample_brems(dr, T, kc, t.u, pr, t.T); break;
+    default: sample_annih(dr, T, t.u, pr); break;
+    }
+    if (pr.local != R(0)) fx.dep += (double)pr.local;
+    int nsec = 0;
+    int sec_k[2];
+    int sec_type[2];
+    R sec_T[2];
+    R sec_u[2][3];
+    for (int k = 0; k < pr.n; ++k) {
+        int st = pr.type[k];
+        R sT = pr.T[k];
+        if (sT < R(p.cut[st])) {
+            fx.dep += (double)sT + rest_energy(st);
+            continue;
+        }
+        sec_type[nsec] = st;
+        sec_T[nsec] = sT;
+        sec_u[nsec][0] = pr.dir[k][0];
+        sec_u[nsec][1] = pr.dir[k][1];
+        sec_u[nsec][2] = pr.dir[k][2];
+        sec_k[nsec] = k;
+        ++nsec;
+    }
+    bool alive = true;
+    if (!pr.parent_alive) {
+        alive = false;
+    } else if (t.T < R(p.cut[t.type])) {
+        fx.dep += (double)t.T + rest_energy(t.type);
+        alive = false;
+    }
+    const uint32_t parent_step = t.step;
+    finish_step(p, t, alive, fx, o);
     for (int k = 0; k < nsec; ++k) {
         int j = o.n;
         o.type[j] = sec_type[k];
@@ -332,17 +369,7 @@ __device__ __forceinline__ void step_track(const Params<R>& p, TrackReg<R>& t, S
         o.step[j] = 0;
         o.n = j + 1;
     }
-    fx.live_delta = nsec - (alive ? 0 : 1);
-}
-
-template <typename R>
-__device__ __forceinline__ void apply_effects(const Params<R>& p, uint32_t ev, uint32_t steps, const Effects& fx)
-{
-    deposit_now(p, ev, fx.vol, fx.dep);
-    if (fx.esc != 0.0) atomicAdd(&p.ledger[3 * (size_t)ev + 0], fx.esc);
-    if (fx.kill != 0.0) atomicAdd(&p.ledger[3 * (size_t)ev + 1], fx.kill);
-    if (fx.finished) finish_track(p, ev, steps);
-    update_live(p, ev, fx.live_delta);
+    fx.live_delta += nsec;
 }
 
 template <typename R>
@@ -380,6 +407,88 @@ __device__ __forceinline__ void store_track(const Tracks<R>& q, long long i, con
     q.tv[i] = pack_tv(type, vol);
 }
 
+template <typename R>
+__device__ __forceinline__ void copy_out(const TrackReg<R>& t, StepOut<R>& o)
+{
+    o.n = 1;
+    o.type[0] = t.type;
+    o.T[0] = t.T;
+    o.u[0][0] = t.u[0];
+    o.u[0][1] = t.u[1];
+    o.u[0][2] = t.u[2];
+    o.uid[0] = t.uid;
+    o.step[0] = t.step;
+}
+
+// warp-aggregated reservation and store of each lane's outputs (all lanes
+// of the warp call it); counts are packed as photons | charged << 16
+template <typename R>
+__device__ __forceinline__ void emit(const Params<R>& p, const Tracks<R>& qo, Counters* cout, int lane,
+                                     const StepOut<R>& o, const double x[3], uint32_t ev, int vol)
+{
+    int ng = 0, nc = 0;
+    for (int k = 0; k < o.n; ++k) {
+        if (o.type[k] == 0)
+            ++ng;
+        else
+            ++nc;
+    }
+    const int v = ng | (nc << 16);
+    int incl = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        int y = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    const int excl = incl - v;
+    const int tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    if (tot == 0) return;
+    int baseG = 0, baseC = 0;
+    if (lane == 31) {
+        int tg = tot & 0xFFFF, tc = tot >> 16;
+        if (tg) baseG = atomicAdd(&cout->n[0], tg);
+        if (tc) baseC = atomicAdd(&cout->n[1], tc);
+    }
+    baseG = __shfl_sync(0xFFFFFFFFu, baseG, 31);
+    baseC = __shfl_sync(0xFFFFFFFFu, baseC, 31);
+    long long og = (long long)baseG + (excl & 0xFFFF);
+    long long oc = (long long)baseC + (excl >> 16);
+    const long long Q = p.Q;
+    for (int k = 0; k < o.n; ++k) {
+        long long dst;
+        if (o.type[k] == 0) {
+            dst = og++;
+        } else {
+            dst = Q - 1 - oc;
+            ++oc;
+        }
+        if (dst < 0 || dst >= Q) {
+            atomicOr(p.status, kStatusQueueOverflow);
+            continue;
+        }
+        store_track(qo, dst, x, o.u[k], o.T[k], o.uid[k], ev, o.step[k], o.type[k], vol);
+    }
+}
+
+// shared-memory records of the tracks that interact in one chunk, sorted by
+// model (structure of arrays)
+template <typename R, int BS>
+struct Staging {
+    double x[3][BS];
+    R u[3][BS];
+    R T[BS];
+    uint64_t uid[BS];
+    double dep[BS];
+    long long src[BS];
+    uint32_t ev[BS];
+    uint32_t step[BS];
+    uint32_t tv[BS];
+    unsigned char model[BS];
+    int count[kNumModels];
+    int offset[kNumModels + 1];
+};
+
+
 // One step-loop iteration over both particle queues of side `side`.
 // Counter slots: cin = this step's input counts, chunk dispenser and
 // growth-token tally; cout = output counts (zero on entry); cclr = slot
@@ -390,11 +499,13 @@ __device__ __forceinline__ void store_track(const Tracks<R>& q, long long i, con
 // only a step with two outputs needs one of the Q - n spare slots: it takes
 // a growth token first, and without one the step is discarded and the track
 // is copied unchanged (its step counter, hence its random stream, is kept).
-// When 2n <= Q every step fits and no token is counted.
-template <typename R>
-__global__ void __launch_bounds__(256) k_step(Params<R> p, int side, int cin, int cout, int cclr)
+// Only interactions make two outputs.  When 2n <= Q every step fits and no
+// token is counted.
+template <typename R, int BS>
+__global__ void __launch_bounds__(BS) k_step(Params<R> p, int side, int cin, int cout, int cclr)
 {
     __shared__ int s_chunk;
+    __shared__ Staging<R, BS> sg;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         p.cnt[cclr].n[0] = 0;
         p.cnt[cclr].n[1] = 0;
@@ -409,33 +520,105 @@ __global__ void __launch_bounds__(256) k_step(Params<R> p, int side, int cin, in
     const long long ntot = (long long)nG + nC;
     const long long spare = Q - ntot;
     const bool unlimited = 2 * ntot <= Q;
-    const int bs = blockDim.x;
+    const int bs = BS;
     const int chunksG = (nG + bs - 1) / bs;
     const int chunksC = (nC + bs - 1) / bs;
-    const int lane = threadIdx.x & 31;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
     const unsigned lanes_below = (1u << lane) - 1u;
+    Counters* const co = &p.cnt[cout];
 
     for (;;) {
-        if (threadIdx.x == 0) s_chunk = atomicAdd(&p.cnt[cin].work, 1);
+        if (tid == 0) s_chunk = atomicAdd(&p.cnt[cin].work, 1);
+        if (tid < kNumModels) sg.count[tid] = 0;
         __syncthreads();
         const int chunk = s_chunk;
-        __syncthreads();
         if (chunk >= chunksG + chunksC) break;
         const bool photon_chunk = chunk < chunksG;
-        const long long i = photon_chunk ? (long long)chunk * bs + threadIdx.x
-                                         : (long long)(chunk - chunksG) * bs + threadIdx.x;
+        const long long i = photon_chunk ? (long long)chunk * bs + tid : (long long)(chunk - chunksG) * bs + tid;
         const long long n_here = photon_chunk ? nG : nC;
         const bool active = i < n_here;
         const long long src = photon_chunk ? i : Q - nC + i;
 
+        // ---- phase A: own track
         TrackReg<R> t;
-        StepOut<R> o;
         Effects fx;
+        StepOut<R> o;
         o.n = 0;
-        bool stepped = false;
+        int model = kNoInteraction;
+        int rank = 0;
         if (active) {
             load_track(qi, src, t);
-            step_track(p, t, o, fx);
+            bool alive;
+            model = transport_part(p, t, fx, alive);
+            if (model == kNoInteraction) {
+                finish_step(p, t, alive, fx, o);
+                apply_effects(p, t.ev, t.step, fx);
+            } else {
+                rank = atomicAdd(&sg.count[model], 1);
+            }
+        }
+        {
+            const unsigned ms = __ballot_sync(0xFFFFFFFFu, active);
+            if (lane == 0 && ms) atomicAdd(&p.total_steps[0], (unsigned long long)__popc(ms));
+        }
+        emit(p, qo, co, lane, o, t.x, t.ev, t.vol);
+        __syncthreads();
+        if (tid == 0) {
+            int acc = 0;
+            for (int m = 0; m < kNumModels; ++m) {
+                sg.offset[m] = acc;
+                acc += sg.count[m];
+            }
+            sg.offset[kNumModels] = acc;
+        }
+        __syncthreads();
+        if (model != kNoInteraction) {
+            const int k = sg.offset[model] + rank;
+            sg.x[0][k] = t.x[0];
+            sg.x[1][k] = t.x[1];
+            sg.x[2][k] = t.x[2];
+            sg.u[0][k] = t.u[0];
+            sg.u[1][k] = t.u[1];
+            sg.u[2][k] = t.u[2];
+            sg.T[k] = t.T;
+            sg.uid[k] = t.uid;
+            sg.dep[k] = fx.dep;
+            sg.src[k] = src;
+            sg.ev[k] = t.ev;
+            sg.step[k] = t.step;
+            sg.tv[k] = pack_tv(t.type, t.vol);
+            sg.model[k] = (unsigned char)model;
+        }
+        __syncthreads();
+
+        // ---- phase B: sampled interactions, sorted by model
+        const int n_int = sg.offset[kNumModels];
+        bool mine = tid < n_int;
+        o.n = 0;
+        bool stepped = false;
+        long long rsrc = 0;
+        if (mine) {
+            t.x[0] = sg.x[0][tid];
+            t.x[1] = sg.x[1][tid];
+            t.x[2] = sg.x[2][tid];
+            t.u[0] = sg.u[0][tid];
+            t.u[1] = sg.u[1][tid];
+            t.u[2] = sg.u[2][tid];
+            t.T = sg.T[tid];
+            t.uid = sg.uid[tid];
+            t.ev = sg.ev[tid];
+            t.step = sg.step[tid];
+            t.type = tv_type(sg.tv[tid]);
+            t.vol = tv_vol(sg.tv[tid]);
+            rsrc = sg.src[tid];
+            fx.dep = sg.dep[tid];
+            fx.esc = 0.0;
+            fx.kill = 0.0;
+            fx.vol = t.vol;
+            fx.finished = false;
+            fx.live_delta = 0;
+            interaction_part(p, t, (int)sg.model[tid], fx, o);
             stepped = true;
         }
         if (!unlimited) {
@@ -453,72 +636,23 @@ __global__ void __launch_bounds__(256) k_step(Params<R> p, int side, int cin, in
                 }
                 got = __shfl_sync(0xFFFFFFFFu, got, leader);
                 if (need && __popc(m & lanes_below) >= got) {
-                    // no room for the second output: discard the step
-                    load_track(qi, src, t);
+                    // no room for the second output: discard the whole step
+                    load_track(qi, rsrc, t);
+                    copy_out(t, o);
                     stepped = false;
                 }
             }
         }
-        if (active && !stepped) {
-            o.n = 1;
-            o.type[0] = t.type;
-            o.T[0] = t.T;
-            o.u[0][0] = t.u[0];
-            o.u[0][1] = t.u[1];
-            o.u[0][2] = t.u[2];
-            o.uid[0] = t.uid;
-            o.step[0] = t.step;
-        }
         if (stepped) apply_effects(p, t.ev, t.step, fx);
         {
-            const unsigned ms = __ballot_sync(0xFFFFFFFFu, stepped);
-            const unsigned md = __ballot_sync(0xFFFFFFFFu, active && !stepped);
-            if (lane == 0) {
-                if (ms) atomicAdd(&p.total_steps[0], (unsigned long long)__popc(ms));
-                if (md) atomicAdd(&p.total_steps[1], (unsigned long long)__popc(md));
+            const unsigned md = __ballot_sync(0xFFFFFFFFu, mine && !stepped);
+            if (lane == 0 && md) {
+                atomicAdd(&p.total_steps[0], -(unsigned long long)__popc(md));
+                atomicAdd(&p.total_steps[1], (unsigned long long)__popc(md));
             }
         }
-        // warp-aggregated reservation: counts packed as g | c << 16
-        int ng = 0, nc = 0;
-        for (int k = 0; k < o.n; ++k) {
-            if (o.type[k] == 0)
-                ++ng;
-            else
-                ++nc;
-        }
-        const int v = ng | (nc << 16);
-        int incl = v;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            int y = __shfl_up_sync(0xFFFFFFFFu, incl, off);
-            if (lane >= off) incl += y;
-        }
-        const int excl = incl - v;
-        const int tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        int baseG = 0, baseC = 0;
-        if (lane == 31) {
-            int tg = tot & 0xFFFF, tc = tot >> 16;
-            if (tg) baseG = atomicAdd(&p.cnt[cout].n[0], tg);
-            if (tc) baseC = atomicAdd(&p.cnt[cout].n[1], tc);
-        }
-        baseG = __shfl_sync(0xFFFFFFFFu, baseG, 31);
-        baseC = __shfl_sync(0xFFFFFFFFu, baseC, 31);
-        long long og = (long long)baseG + (excl & 0xFFFF);
-        long long oc = (long long)baseC + (excl >> 16);
-        for (int k = 0; k < o.n; ++k) {
-            long long dst;
-            if (o.type[k] == 0) {
-                dst = og++;
-            } else {
-                dst = Q - 1 - oc;
-                ++oc;
-            }
-            if (dst < 0 || dst >= Q) {
-                atomicOr(p.status, kStatusQueueOverflow);
-                continue;
-            }
-            store_track(qo, dst, t.x, o.u[k], o.T[k], o.uid[k], t.ev, o.step[k], o.type[k], t.vol);
-        }
+        emit(p, qo, co, lane, o, t.x, t.ev, t.vol);
+        __syncthreads();
     }
 }
 

@@ -52,5 +52,5 @@ def test_pool_size_and_options_without_gpu():
     o.precision = 1
     n3 = L.emt_pool_bytes(ctypes.byref(o))
     assert n2 - n3 >= 2 * 16 * (1 << 23)
-    o.block_size = 48
+    o.block_size = 96
     assert L.emt_pool_bytes(ctypes.byref(o)) == 0  # invalid options

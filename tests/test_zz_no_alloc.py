@@ -62,7 +62,8 @@ def test_static_entry_point_matches_context_path_twice():
         torch.cuda.synchronize()
         h, sm = hist.cpu().numpy(), summ.cpu().numpy()
         e_in = want_summ[:, 3]
-        assert np.array_equal(sm[:, 3], e_in)
+        # e_in of a multi-primary event is an FP64 atomic sum: order-dependent rounding
+        assert np.all(np.abs(sm[:, 3] - e_in) <= 1e-14 * e_in)
         assert np.all(np.abs(sm[:, 0] - want_summ[:, 0]) <= TOL * e_in), f"call {call}"
         assert np.all(np.abs(h - want_hist).max(axis=1) <= TOL * e_in), f"call {call}"
         assert np.array_equal(sm[:, 4:], want_summ[:, 4:]), f"call {call}: step/track counts"
