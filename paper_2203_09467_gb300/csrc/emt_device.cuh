@@ -426,40 +426,72 @@ __device__ __forceinline__ Exit nav_exit(const Params<R>& p, int vol, const doub
 
 // ------------------------------------------------------------------ field
 // classical RK4 in path length on (x, u), du/ds = kq u x B, |p| fixed
-// during the step; u renormalised after each substep
+// during the step; u renormalised after each substep.  The direction and
+// its derivatives are evaluated in R (FP64 path: double, in the operation
+// order of the definition; mixed path: float), positions accumulate in FP64.
 template <typename R>
-__device__ __forceinline__ void rk4(const Params<R>& p, double kq, const double x[3], const double u[3], double hs,
-                                    double xo[3], double uo[3])
+__device__ __forceinline__ void rk4(const Params<R>& p, R kq, const double x[3], const R u[3], R hs, double xo[3],
+                                    R uo[3])
 {
-    const double* B = p.B;
-    double a1[3], a2[3], a3[3], a4[3], u2[3], u3[3], u4[3];
-    a1[0] = kq * (u[1] * B[2] - u[2] * B[1]);
-    a1[1] = kq * (u[2] * B[0] - u[0] * B[2]);
-    a1[2] = kq * (u[0] * B[1] - u[1] * B[0]);
+    const R B0 = R(p.B[0]), B1 = R(p.B[1]), B2 = R(p.B[2]);
+    R a1[3], a2[3], a3[3], a4[3], u2[3], u3[3], u4[3];
+    a1[0] = kq * (u[1] * B2 - u[2] * B1);
+    a1[1] = kq * (u[2] * B0 - u[0] * B2);
+    a1[2] = kq * (u[0] * B1 - u[1] * B0);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) u2[i] = u[i] + 0.5 * hs * a1[i];
-    a2[0] = kq * (u2[1] * B[2] - u2[2] * B[1]);
-    a2[1] = kq * (u2[2] * B[0] - u2[0] * B[2]);
-    a2[2] = kq * (u2[0] * B[1] - u2[1] * B[0]);
+    for (int i = 0; i < 3; ++i) u2[i] = u[i] + R(0.5) * hs * a1[i];
+    a2[0] = kq * (u2[1] * B2 - u2[2] * B1);
+    a2[1] = kq * (u2[2] * B0 - u2[0] * B2);
+    a2[2] = kq * (u2[0] * B1 - u2[1] * B0);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) u3[i] = u[i] + 0.5 * hs * a2[i];
-    a3[0] = kq * (u3[1] * B[2] - u3[2] * B[1]);
-    a3[1] = kq * (u3[2] * B[0] - u3[0] * B[2]);
-    a3[2] = kq * (u3[0] * B[1] - u3[1] * B[0]);
+    for (int i = 0; i < 3; ++i) u3[i] = u[i] + R(0.5) * hs * a2[i];
+    a3[0] = kq * (u3[1] * B2 - u3[2] * B1);
+    a3[1] = kq * (u3[2] * B0 - u3[0] * B2);
+    a3[2] = kq * (u3[0] * B1 - u3[1] * B0);
 #pragma unroll
     for (int i = 0; i < 3; ++i) u4[i] = u[i] + hs * a3[i];
-    a4[0] = kq * (u4[1] * B[2] - u4[2] * B[1]);
-    a4[1] = kq * (u4[2] * B[0] - u4[0] * B[2]);
-    a4[2] = kq * (u4[0] * B[1] - u4[1] * B[0]);
-    double h6 = hs / 6.0;
+    a4[0] = kq * (u4[1] * B2 - u4[2] * B1);
+    a4[1] = kq * (u4[2] * B0 - u4[0] * B2);
+    a4[2] = kq * (u4[0] * B1 - u4[1] * B0);
+    R h6 = hs / R(6);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        xo[i] = x[i] + h6 * (u[i] + 2.0 * u2[i] + 2.0 * u3[i] + u4[i]);
-        uo[i] = u[i] + h6 * (a1[i] + 2.0 * a2[i] + 2.0 * a3[i] + a4[i]);
+        xo[i] = x[i] + (double)(h6 * (u[i] + R(2) * u2[i] + R(2) * u3[i] + u4[i]));
+        uo[i] = u[i] + h6 * (a1[i] + R(2) * a2[i] + R(2) * a3[i] + a4[i]);
     }
-    double n = sqrt(uo[0] * uo[0] + uo[1] * uo[1] + uo[2] * uo[2]);
+    R n = msqrt(uo[0] * uo[0] + uo[1] * uo[1] + uo[2] * uo[2]);
 #pragma unroll
     for (int i = 0; i < 3; ++i) uo[i] = uo[i] / n;
+}
+
+// True when the chord from x (inside volume vol) to x1 cannot leave vol:
+// x1 lies inside the volume by more than kChordMargin, and in the world
+// vacuum the chord's bounding box also stays kChordMargin away from the
+// layer stack.  nav_exit would then return t > 1 for this chord (the exact
+// exit parameter exceeds 1 by at least margin/|c|, far above rounding), so
+// skipping it changes no result.
+constexpr double kChordMargin = 1e-6;  // cm
+
+template <typename R>
+__device__ __forceinline__ bool chord_inside(const Params<R>& p, int vol, const double x[3], const double x1[3])
+{
+    const double m = kChordMargin;
+    if (vol >= 0) {
+        return x1[2] > p.zb[vol] + m && x1[2] < p.zb[vol + 1] - m && x1[0] > -p.hx + m && x1[0] < p.hx - m &&
+               x1[1] > -p.hy + m && x1[1] < p.hy - m;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        if (!(x1[a] > p.wlo[a] + m && x1[a] < p.whi[a] - m)) return false;
+    const double lo[3] = {-p.hx - m, -p.hy - m, p.zb[0] - m};
+    const double hi[3] = {p.hx + m, p.hy + m, p.zb[p.n_layers] + m};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double smin = x[a] < x1[a] ? x[a] : x1[a];
+        const double smax = x[a] < x1[a] ? x1[a] : x[a];
+        if (smax < lo[a] || smin > hi[a]) return true;  // separated along axis a
+    }
+    return false;
 }
 
 // substeps of equal length smax/ceil(smax/hmax), hmax = sqrt(8 r delta);
@@ -468,7 +500,7 @@ __device__ __forceinline__ void rk4(const Params<R>& p, double kq, const double 
 // plane.  Returns the path length.
 template <typename R>
 __device__ __forceinline__ double propagate_field(const Params<R>& p, int charge, double T, int vol, double x[3],
-                                                  double u[3], double smax, Exit* bnd, bool* crossed)
+                                                  R u[3], double smax, Exit* bnd, bool* crossed)
 {
     double pm = sqrt(T * (T + 2.0 * kMe));
     double kq = charge * kFieldC / pm;
@@ -481,24 +513,27 @@ __device__ __forceinline__ double propagate_field(const Params<R>& p, int charge
     double s = 0.0;
     *crossed = false;
     for (long long i = 0; i < n; ++i) {
-        double x1[3], u1[3], c[3];
-        rk4(p, kq, x, u, hs, x1, u1);
+        double x1[3], c[3];
+        R u1[3];
+        rk4(p, R(kq), x, u, R(hs), x1, u1);
+        if (!chord_inside(p, vol, x, x1)) {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) c[a] = x1[a] - x[a];
-        Exit e = nav_exit(p, vol, x, c);
-        if (e.t <= 1.0) {
-            double h2 = hs * e.t;
-            rk4(p, kq, x, u, h2, x1, u1);
-            x1[e.axis] = e.plane;
+            for (int a = 0; a < 3; ++a) c[a] = x1[a] - x[a];
+            Exit e = nav_exit(p, vol, x, c);
+            if (e.t <= 1.0) {
+                double h2 = hs * e.t;
+                rk4(p, R(kq), x, u, R(h2), x1, u1);
+                x1[e.axis] = e.plane;
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                x[a] = x1[a];
-                u[a] = u1[a];
+                for (int a = 0; a < 3; ++a) {
+                    x[a] = x1[a];
+                    u[a] = u1[a];
+                }
+                s += h2;
+                *bnd = e;
+                *crossed = true;
+                return s;
             }
-            s += h2;
-            *bnd = e;
-            *crossed = true;
-            return s;
         }
 #pragma unroll
         for (int a = 0; a < 3; ++a) {

@@ -220,11 +220,8 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
             interact = false;
         }
         bool crossed = false;
-        s = propagate_field(p, t.type == 1 ? -1 : 1, (double)t.T, t.vol, t.x, ud, smax, &e, &crossed);
+        s = propagate_field(p, t.type == 1 ? -1 : 1, (double)t.T, t.vol, t.x, t.u, smax, &e, &crossed);
         boundary = crossed;
-        t.u[0] = R(ud[0]);
-        t.u[1] = R(ud[1]);
-        t.u[2] = R(ud[2]);
     }
     if (boundary) interact = false;
 
@@ -502,7 +499,7 @@ struct Staging {
 // Only interactions make two outputs.  When 2n <= Q every step fits and no
 // token is counted.
 template <typename R, int BS>
-__global__ void __launch_bounds__(BS) k_step(Params<R> p, int side, int cin, int cout, int cclr)
+__global__ void __launch_bounds__(BS, 512 / BS) k_step(Params<R> p, int side, int cin, int cout, int cclr)
 {
     __shared__ int s_chunk;
     __shared__ Staging<R, BS> sg;
