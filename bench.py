@@ -67,6 +67,11 @@ def workload(name, n_events, rank):
         s.seed = 4
         prim = W.batched_primaries(n_events, seed=4 + 7919 * rank)
         desc = f"calorimeter in 2 T field, {n_events} events of 1-64 primaries, 0.1-100 GeV"
+    elif name == "served":
+        s = W.calo_field_setup()
+        s.seed = 5
+        prim = W.served_primaries(n_events, seed=5 + 7919 * rank)
+        desc = f"calorimeter in 2 T field, {n_events} requests of 1-100 primaries, 1-50 GeV"
     else:
         raise SystemExit(f"unknown workload {name}")
     ids = (np.arange(n_events, dtype=np.uint64) + np.uint64(rank * n_events))
@@ -194,9 +199,17 @@ def gpu_arm(args):
 
     setup, prim, ids, desc = workload(args.workload, args.events, rank)
     n = len(ids)
-    ctx = emt.context_for(setup, device=local, precision=args.precision, loop_mode=args.loop,
-                          graph_steps=args.graph_steps, slot_capacity=args.slots, max_events=n,
-                          block_size=args.block)
+    tune = None
+    if args.loop == "auto":
+        from paper_2203_09467_gb300 import autotune
+        best, timings = autotune.autotune(args.workload, setup, prim, ids, args.precision, use_cache=not args.retune,
+                                          slot_capacity=args.slots, device=local)
+        cfg = dict(best)
+        tune = {"best": best, "ms_per_candidate": timings}
+    else:
+        cfg = {"block_size": args.block, "loop_mode": args.loop, "graph_steps": args.graph_steps}
+    ctx = emt.context_for(setup, device=local, precision=args.precision, slot_capacity=args.slots, max_events=n,
+                          **cfg)
     stream = ctx.stream
     dev = torch.device("cuda", local)
     dprim = {k: torch.as_tensor(v).to(dev) for k, v in prim.items()}
@@ -298,6 +311,32 @@ def gpu_arm(args):
     if args.traffic_per_launch:
         roof["traffic"] = args.traffic_per_launch
 
+    # the plain form: the same events submitted and run one at a time
+    forms = None
+    if args.one_at_a_time > 0 and rank == 0:
+        k = min(args.one_at_a_time, n)
+        single = emt.context_for(setup, device=local, precision=args.precision, slot_capacity=1 << 22,
+                                 max_events=1, block_size=cfg["block_size"], loop_mode="plain")
+        steps1 = 0
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(single.stream)
+        for e in range(k):
+            sub = {kk: v[e:e + 1] for kk, v in dprim.items()}
+            sub["event"] = torch.zeros(1, dtype=torch.int32, device=dev)
+            single.submit(ids[e:e + 1], sub)
+            steps1 += single.run()["track_steps"]
+            single.read_all(hist_d[e:e + 1], summ_d[e:e + 1])
+        b.record(single.stream)
+        b.synchronize()
+        t1 = a.elapsed_time(b) / 1e3
+        single.close()
+        forms = {"batched": {"events_per_s": n / (total_ms / 1e3 / args.steps), "track_steps_per_s": value / world,
+                             "config": cfg},
+                 "one_at_a_time": {"events_per_s": k / t1, "track_steps_per_s": steps1 / t1,
+                                   "sample_events": k}}
+
     ctx.close()
     if rank != 0:
         if world > 1:
@@ -309,7 +348,8 @@ def gpu_arm(args):
         "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
         "data": "synthetic",
-        "config": {"workload": desc, "precision": args.precision, "loop": args.loop,
+        "config": {"workload": desc, "precision": args.precision, "loop": cfg["loop_mode"],
+                   "graph_steps": cfg["graph_steps"], "block": cfg["block_size"] or 256,
                    "slot_capacity": args.slots, "events_per_gpu": n,
                    "l2": "512 MB buffer written between timed steps; track state >> L2"},
         "events_per_s": n * world / (total_ms_all / 1e3 / args.steps),
@@ -319,6 +359,10 @@ def gpu_arm(args):
         "roofline": roof,
         "clocks": clk,
     }
+    if forms:
+        line["forms"] = forms
+    if tune:
+        line["autotune"] = tune
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(setup, prim, ids, budget_s=args.cpu_budget)
     print(json.dumps(line), flush=True)
@@ -327,19 +371,69 @@ def gpu_arm(args):
         dist.destroy_process_group()
 
 
+def served_arm(args):
+    """Event requests arriving as a Poisson process at each rate; continuous
+    batching against the one-batch-at-a-time schedule on the same GPU.
+    Latency = completion - arrival (host monotonic clock)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2203_09467_gb300 import emt
+
+    setup = W.calo_field_setup()
+    setup.seed = 5
+    rates = [float(r) for r in args.rates.split(",")]
+    results = []
+    for ri, rate in enumerate(rates):
+        arrival = W.poisson_arrivals(rate, args.duration, seed=5 + ri)
+        n = len(arrival)
+        prim = W.served_primaries(n, seed=5 + ri)
+        ids = np.arange(n, dtype=np.uint64) + np.uint64(1_000_000 * ri)
+        row = {"rate_hz": rate, "requests": n, "duration_s": args.duration}
+        for mode in ("continuous", "batch"):
+            ctx = emt.context_for(setup, precision=args.precision, slot_capacity=args.serve_slots,
+                                  max_events=args.serve_events, loop_mode="graph", graph_steps=6)
+            admit, done, hist, summ = ctx.serve(ids, arrival, prim, mode=mode, steps_per_poll=6)
+            ctx.close()
+            lat = done - arrival
+            span = done.max() - arrival.min()
+            row[mode] = {"events_per_s": n / span, "p50_latency_s": float(np.percentile(lat, 50)),
+                         "p99_latency_s": float(np.percentile(lat, 99)),
+                         "mean_queue_s": float(np.mean(admit - arrival)),
+                         "track_steps": float(summ[:, 4].sum())}
+        results.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    top = results[-1]
+    line = {"metric": "events/s", "value": top["continuous"]["events_per_s"], "unit": "events/s", "n_gpus": 1,
+            "steps": len(rates), "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+            "config": {"workload": "served: Poisson requests of 1-100 primaries (e-/e+/gamma, 1-50 GeV) on the "
+                                   "calorimeter in a 2 T field", "precision": args.precision,
+                       "track_slots": args.serve_slots, "event_slots": args.serve_events},
+            "rates": results}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="emt", choices=["emt", "reference"])
-    ap.add_argument("--workload", default="calo", choices=["calo", "slab", "calo_field", "batched"])
+    ap.add_argument("--workload", default="calo", choices=["calo", "slab", "calo_field", "batched", "served"])
+    ap.add_argument("--rates", default="10,100,1000", help="served: request rates (Hz)")
+    ap.add_argument("--duration", type=float, default=60.0, help="served: seconds of requests per rate")
+    ap.add_argument("--serve-slots", type=int, default=1 << 22, help="served: track-slot pool")
+    ap.add_argument("--serve-events", type=int, default=4096, help="served: event slots")
     ap.add_argument("--events", type=int, default=10000)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--loop", default="plain", choices=["plain", "graph"])
+    ap.add_argument("--loop", default="auto", choices=["auto", "plain", "graph"],
+                    help="auto: autotune block size and loop driver on the workload first")
+    ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")
     ap.add_argument("--graph-steps", type=int, default=12)
     ap.add_argument("--slots", type=int, default=1 << 25)
     ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--one-at-a-time", type=int, default=100,
+                    help="events of the plain one-event-at-a-time form to time (0: skip)")
     ap.add_argument("--ref-events", type=int, default=1000)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -348,6 +442,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload == "served":
+        served_arm(args)
     else:
         gpu_arm(args)
 

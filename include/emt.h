@@ -206,6 +206,40 @@ emt_status emt_read_event(emt_ctx* ctx, uint64_t event_id, double* hist, double*
 emt_status emt_read_all(emt_ctx* ctx, double* hist, double* summary, uint64_t* ids, int32_t where);
 int32_t emt_events_in_flight(const emt_ctx* ctx);
 
+/* ---------------------------------------------------------------------
+ * Serving (Sec. 3.4: many concurrent events keep the device busy; Sec. 4:
+ * workflows must batch events).  emt_serve replays a stream of event
+ * requests against one context in real time (arrival times divided by
+ * time_scale) and returns when every request has been answered.
+ *   EMT_SERVE_CONTINUOUS: requests are admitted as soon as event slots and
+ *     track slots allow, while earlier events are still in flight; the step
+ *     loop advances steps_per_poll iterations between admissions and
+ *     finished events are read back immediately (continuous batching).
+ *   EMT_SERVE_BATCH: one batch at a time: whenever no event is in flight,
+ *     every request that has arrived is admitted and run to completion.
+ * host arrays, n_events entries in arrival order: event_ids (distinct, none
+ * in flight), arrival_s (non-decreasing), first/count (the request's
+ * primaries are prim[first .. first+count), requests contiguous and in
+ * order); prim: host primaries as in emt_submit (its `event` field is
+ * ignored).  Outputs (host): admit_s, done_s (seconds since the call
+ * started; admit_s may be NULL), hist[n_events][n_bins] and
+ * summary[n_events][6] (either may be NULL).  The loop uses only the entry
+ * points above and leaves the context empty.
+ * --------------------------------------------------------------------- */
+#define EMT_SERVE_CONTINUOUS 0
+#define EMT_SERVE_BATCH 1
+
+typedef struct emt_serve_options {
+    int32_t mode;           /* EMT_SERVE_* */
+    int32_t steps_per_poll; /* iterations between admissions (continuous) */
+    int32_t n_bins;         /* histogram width of hist (the geometry's n_bins) */
+    double time_scale;      /* 1 = real time; > 1 replays faster */
+} emt_serve_options;
+
+emt_status emt_serve(emt_ctx* ctx, int32_t n_events, const uint64_t* event_ids, const double* arrival_s,
+                     const int32_t* first, const int32_t* count, const emt_primaries* prim,
+                     const emt_serve_options* opt, double* admit_s, double* done_s, double* hist, double* summary);
+
 /* Diagnostics: copy table (material m, particle p, quantity q) to host
  * out[n] (n = grid size).  gamma q: 0 photo, 1 compton, 2 pair;
  * e-: 0 ioni, 1 brems, 3 range; e+: 0 ioni, 1 brems, 2 annih, 3 range;

@@ -1,0 +1,88 @@
+"""Autotuner of the step-loop launch configuration.
+
+The tunable knobs are the step kernel's block size (128 or 256 threads: a
+larger block regroups more interacting tracks per model, a smaller one
+leaves more blocks per SM) and the step-loop driver (a host loop with one
+counter read per step, or CUDA graphs of 6, 12 or 24 steps with one counter
+read per graph).  Every candidate transports the same batch of events; the
+fastest by CUDA-event time wins.  Results are cached per GPU name, workload
+name and precision in a JSON file next to this module.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+
+from . import emt
+
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_autotune_cache.json")
+
+CANDIDATES = [
+    {"block_size": b, "loop_mode": loop, "graph_steps": k}
+    for b in (128, 256)
+    for loop, k in (("plain", 12), ("graph", 6), ("graph", 12), ("graph", 24))
+]
+
+
+def _key(name, precision):
+    import torch
+    return f"{torch.cuda.get_device_name()}|{name}|{precision}"
+
+
+def time_config(setup, prim, ids, precision, cfg, repeats=2, slot_capacity=1 << 25, device=0):
+    """Best-of-`repeats` milliseconds of one full transport of the batch."""
+    import torch
+    ctx = emt.context_for(setup, device=device, precision=precision, slot_capacity=slot_capacity,
+                          max_events=len(ids), **cfg)
+    dprim = {k: torch.as_tensor(v).to(ctx.device) for k, v in prim.items()}
+    hist = torch.empty((len(ids), setup.n_bins), dtype=torch.float64, device=ctx.device)
+    summ = torch.empty((len(ids), 6), dtype=torch.float64, device=ctx.device)
+    best = float("inf")
+    for _ in range(repeats + 1):  # the first pass warms up (and captures the graph)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(ctx.stream)
+        ctx.submit(ids, dprim)
+        ctx.run()
+        ctx.read_all(hist, summ)
+        b.record(ctx.stream)
+        b.synchronize()
+        best = min(best, a.elapsed_time(b))
+    ctx.close()
+    return best
+
+
+def autotune(name, setup, prim, ids, precision="fp64", use_cache=True, repeats=2, slot_capacity=1 << 25,
+             device=0, candidates=None):
+    """Return (best configuration, {candidate: ms}) for this workload."""
+    key = _key(name, precision)
+    cache = {}
+    if use_cache and os.path.exists(CACHE):
+        try:
+            cache = json.load(open(CACHE))
+        except Exception:
+            cache = {}
+    if use_cache and key in cache:
+        return cache[key]["best"], cache[key]["timings"]
+    timings = {}
+    best, best_ms = None, float("inf")
+    for cfg in candidates or CANDIDATES:
+        ms = time_config(setup, prim, ids, precision, cfg, repeats, slot_capacity, device)
+        timings[json.dumps(cfg, sort_keys=True)] = ms
+        if ms < best_ms:
+            best, best_ms = cfg, ms
+    cache[key] = {"best": best, "timings": timings}
+    try:
+        with open(CACHE, "w") as f:
+            json.dump(cache, f, indent=1)
+    except OSError:
+        pass
+    return best, timings
+
+
+def sample_ids(n, k, seed=0):
+    """k event indices of n, sorted (for tuning on a sample)."""
+    return np.sort(np.random.default_rng(seed).choice(n, size=min(k, n), replace=False))

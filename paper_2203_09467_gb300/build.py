@@ -24,6 +24,7 @@ UNITS = {
     "emt_tables.cu": ["--fmad=false"],
     "emt_kernels_fp64.cu": ["--fmad=false"],
     "emt_kernels_mixed.cu": [],
+    "emt_serve.cu": [],
 }
 
 

@@ -62,6 +62,14 @@ class Primaries(ctypes.Structure):
                 ("T_MeV", ctypes.c_void_p), ("pos_cm", ctypes.c_void_p), ("dir", ctypes.c_void_p)]
 
 
+class ServeOptions(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("steps_per_poll", ctypes.c_int32), ("n_bins", ctypes.c_int32),
+                ("time_scale", ctypes.c_double)]
+
+
+SERVE = {"continuous": 0, "batch": 1}
+
+
 class RunStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int64), ("track_steps", ctypes.c_int64), ("peak_tracks", ctypes.c_int64),
                 ("deferred", ctypes.c_int64), ("live_tracks", ctypes.c_int64), ("state_bytes", ctypes.c_int64),
@@ -95,6 +103,10 @@ _SIGS = {
                                               ctypes.c_void_p]),
     "emt_debug_get_tracks": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]),
+    "emt_serve": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(Primaries),
+                                   ctypes.POINTER(ServeOptions), ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p]),
     "emt_transport_static": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_uint32, ctypes.POINTER(Material),
                                               ctypes.c_int32, ctypes.POINTER(Physics), ctypes.POINTER(Layer),
                                               ctypes.c_int32, ctypes.POINTER(World), ctypes.c_int32,
@@ -307,6 +319,30 @@ class Context:
             summary = np.zeros((n, 6))
         self._check(lib().emt_read_all(self._h, _ptr(hist), _ptr(summary), _ptr(ids), HOST))
         return hist, summary, ids[:n]
+
+    def serve(self, event_ids, arrival_s, prim, mode: str = "continuous", steps_per_poll: int = 8,
+              time_scale: float = 1.0):
+        """Replay a request stream (emt_serve).  prim: host primaries grouped
+        by event in arrival order.  Returns admit_s, done_s, hist, summary."""
+        ids = np.ascontiguousarray(event_ids, np.uint64)
+        arr = np.ascontiguousarray(arrival_s, np.float64)
+        n = len(ids)
+        ev = np.asarray(prim["event"])
+        count = np.bincount(ev, minlength=n).astype(np.int32)
+        first = np.concatenate([[0], np.cumsum(count)[:-1]]).astype(np.int32)
+        keep = {"type": np.ascontiguousarray(prim["type"], np.int32), "T": np.ascontiguousarray(prim["T"], np.float64),
+                "pos": np.ascontiguousarray(prim["pos"], np.float64), "dir": np.ascontiguousarray(prim["dir"], np.float64),
+                "event": np.ascontiguousarray(ev, np.int32)}
+        p = Primaries(len(keep["T"]), _ptr(keep["event"]), _ptr(keep["type"]), _ptr(keep["T"]), _ptr(keep["pos"]),
+                      _ptr(keep["dir"]))
+        o = ServeOptions(SERVE[mode], int(steps_per_poll), int(self.n_bins), float(time_scale))
+        admit = np.zeros(n)
+        done = np.zeros(n)
+        hist = np.zeros((n, self.n_bins))
+        summ = np.zeros((n, 6))
+        self._check(lib().emt_serve(self._h, n, _ptr(ids), _ptr(arr), _ptr(first), _ptr(count), ctypes.byref(p),
+                                    ctypes.byref(o), _ptr(admit), _ptr(done), _ptr(hist), _ptr(summ)))
+        return admit, done, hist, summ
 
     # -- diagnostics
     def get_table(self, m: int, p: int, q: int) -> np.ndarray:
