@@ -205,6 +205,8 @@ emt_status emt_read_event(emt_ctx* ctx, uint64_t event_id, double* hist, double*
  * ids (host, may be NULL) receives the event ids. */
 emt_status emt_read_all(emt_ctx* ctx, double* hist, double* summary, uint64_t* ids, int32_t where);
 int32_t emt_events_in_flight(const emt_ctx* ctx);
+/* Tracks waiting for their next step (as of the last call). */
+int64_t emt_tracks_in_flight(const emt_ctx* ctx);
 
 /* ---------------------------------------------------------------------
  * Serving (Sec. 3.4: many concurrent events keep the device busy; Sec. 4:
@@ -234,6 +236,8 @@ typedef struct emt_serve_options {
     int32_t steps_per_poll; /* iterations between admissions (continuous) */
     int32_t n_bins;         /* histogram width of hist (the geometry's n_bins) */
     double time_scale;      /* 1 = real time; > 1 replays faster */
+    int64_t admit_below;    /* admit new requests only while fewer tracks are in
+                               flight (room for showers to grow); <= 0: no limit */
 } emt_serve_options;
 
 emt_status emt_serve(emt_ctx* ctx, int32_t n_events, const uint64_t* event_ids, const double* arrival_s,

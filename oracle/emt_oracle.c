@@ -1092,6 +1092,12 @@ int orc_sample(int process, double E, double cut_e, double cut_g, uint32_t seed,
 /* (Sec. 3.3 says only that propagation is on-device with selectable   */
 /* integrators; this is a reading.)                                    */
 /* ------------------------------------------------------------------ */
+/* A step in a field takes at most MAX_SUBSTEPS substeps of h_max (and at
+ * most max_field_step); a step shortened this way ends without an
+ * interaction and the track continues at its next step (a reading: it
+ * bounds the work of one step of a looping low-energy track). */
+#define MAX_SUBSTEPS 100
+
 static void cross(const double a[3], const double b[3], double o[3])
 {
     o[0] = a[1] * b[2] - a[2] * b[1];
@@ -1264,6 +1270,16 @@ static void step_track(const orc_handle* h, uint64_t event_id, track_t* tr, tall
         double smax = s_phys;
         if (smax > h->max_field_step) {
             smax = h->max_field_step;
+            interact = 0;
+        }
+        /* at most MAX_SUBSTEPS RK4 substeps per step (the substep length
+         * h_max below is the one propagate_field uses) */
+        double pm = sqrt(tr->T * (tr->T + 2.0 * ME));
+        double bmag = sqrt(h->B[0] * h->B[0] + h->B[1] * h->B[1] + h->B[2] * h->B[2]);
+        double hmax = sqrt(8.0 * (pm / (FIELD_C * bmag)) * h->rk_delta);
+        double cap = MAX_SUBSTEPS * hmax;
+        if (smax > cap) {
+            smax = cap;
             interact = 0;
         }
         int crossed = 0;

@@ -140,11 +140,16 @@ struct emt_ctx {
     std::unordered_map<uint64_t, int> id_to_slot;
     std::vector<int> order;  // slots in submission order
     unsigned done_seen = 0;
+    // host mirrors valid while no device work has run since they were read
+    unsigned long long steps_seen[2] = {0, 0};  // total step counters
+    unsigned head_cached = 0;                    // finished-event ring head
+    bool head_fresh = false;
     // pinned host mirrors
     Counters* h_cnt = nullptr;
     int* h_status = nullptr;
     unsigned long long* h_steps = nullptr;
     unsigned* h_done = nullptr;
+    char* h_misc = nullptr;  // status .. done_head, read in one copy
     // CUDA graph of graph_steps iterations
     cudaGraphExec_t graph = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -341,9 +346,8 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
     emt_run_stats s;
     std::memset(&s, 0, sizeof s);
     const Plan& pl = c->plan;
-    EMT_CUDA(c, cudaMemcpyAsync(c->h_steps, c->pool + pl.total_steps, 16, cudaMemcpyDeviceToHost, c->stream));
-    EMT_CUDA(c, cudaStreamSynchronize(c->stream));
-    const unsigned long long steps0 = c->h_steps[0], def0 = c->h_steps[1];
+    c->head_fresh = false;
+    const unsigned long long steps0 = c->steps_seen[0], def0 = c->steps_seen[1];
     unsigned long long last_steps = steps0;
     const int64_t live0 = c->live_g + c->live_c;
     int64_t peak = live0;
@@ -427,11 +431,22 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
             if (r != EMT_OK) return r;
         }
     }
-    EMT_CUDA(c, cudaMemcpyAsync(c->h_steps, c->pool + pl.total_steps, 16, cudaMemcpyDeviceToHost, c->stream));
-    emt_status r = sync_status(c, "emt_run");
-    if (r != EMT_OK) return r;
-    s.track_steps = (int64_t)(c->h_steps[0] - steps0);
-    s.deferred = (int64_t)(c->h_steps[1] - def0);
+    // status word, step counters and finished-event head in one copy
+    const size_t misc = pl.done_head + sizeof(unsigned) - pl.status;
+    EMT_CUDA(c, cudaMemcpyAsync(c->h_misc, c->pool + pl.status, misc, cudaMemcpyDeviceToHost, c->stream));
+    EMT_CUDA(c, cudaStreamSynchronize(c->stream));
+    const int status = *reinterpret_cast<const int*>(c->h_misc);
+    const unsigned long long* steps = reinterpret_cast<const unsigned long long*>(c->h_misc + (pl.total_steps - pl.status));
+    c->steps_seen[0] = steps[0];
+    c->steps_seen[1] = steps[1];
+    c->head_cached = *reinterpret_cast<const unsigned*>(c->h_misc + (pl.done_head - pl.status));
+    c->head_fresh = true;
+    if (status & (int)kStatusQueueOverflow) {
+        c->poisoned = true;
+        return fail(c, EMT_ERR_CUDA, "emt_run: track queue overflow (internal error)");
+    }
+    s.track_steps = (int64_t)(c->steps_seen[0] - steps0);
+    s.deferred = (int64_t)(c->steps_seen[1] - def0);
     s.peak_tracks = peak;
     s.live_tracks = c->live_g + c->live_c;
     s.kernel_ms = kernel_ms;
@@ -458,9 +473,14 @@ emt_status check_ready(emt_ctx* c)
 emt_status drain_done(emt_ctx* c)
 {
     const Plan& pl = c->plan;
-    EMT_CUDA(c, cudaMemcpyAsync(c->h_done, c->pool + pl.done_head, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
-    EMT_CUDA(c, cudaStreamSynchronize(c->stream));
-    unsigned head = *c->h_done;
+    unsigned head = c->head_cached;
+    if (!c->head_fresh) {
+        EMT_CUDA(c, cudaMemcpyAsync(c->h_done, c->pool + pl.done_head, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                    c->stream));
+        EMT_CUDA(c, cudaStreamSynchronize(c->stream));
+        head = *c->h_done;
+        c->head_cached = head;
+    }
     if (head == c->done_seen) return EMT_OK;
     unsigned n = head - c->done_seen;
     if (n > (unsigned)pl.max_events) return fail(c, EMT_ERR_CUDA, "finished-event ring overrun");
@@ -541,7 +561,9 @@ emt_status emt_create(const emt_options* o, emt_ctx** out)
     if (cudaMallocHost((void**)&c->h_cnt, sizeof(Counters)) != cudaSuccess ||
         cudaMallocHost((void**)&c->h_status, sizeof(int)) != cudaSuccess ||
         cudaMallocHost((void**)&c->h_steps, 2 * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMallocHost((void**)&c->h_done, sizeof(unsigned)) != cudaSuccess)
+        cudaMallocHost((void**)&c->h_done, sizeof(unsigned)) != cudaSuccess ||
+        cudaMallocHost((void**)&c->h_misc, make_plan(*o).done_head + sizeof(unsigned) - make_plan(*o).status) !=
+            cudaSuccess)
         return bail(EMT_ERR_CUDA);
     if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) return bail(EMT_ERR_CUDA);
     const Plan& pl = c->plan;
@@ -575,6 +597,7 @@ void emt_destroy(emt_ctx* c)
     if (c->h_status) cudaFreeHost(c->h_status);
     if (c->h_steps) cudaFreeHost(c->h_steps);
     if (c->h_done) cudaFreeHost(c->h_done);
+    if (c->h_misc) cudaFreeHost(c->h_misc);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -788,6 +811,7 @@ static emt_status submit_impl(emt_ctx* c, int32_t n_events, const uint64_t* ids,
     EMT_CUDA(c, cudaGetLastError());
     Params<R>& p = params<R>(c);
     int side = (int)(c->it & 1), cs = (int)(c->it % 3);
+    c->head_fresh = false;  // admission may finish events (token release)
     EMT_CUDA(c, Launch<R>::admit(p, side, cs, n, c->at<int32_t>(pl.st_ev), c->at<int32_t>(pl.st_type),
                                  c->at<double>(pl.st_T), c->at<double>(pl.st_pos), c->at<double>(pl.st_dir),
                                  c->at<uint32_t>(pl.st_slot), c->at<uint32_t>(pl.st_uid), st));
@@ -925,6 +949,8 @@ emt_status emt_read_all(emt_ctx* c, double* hist, double* summary, uint64_t* ids
 
 int32_t emt_events_in_flight(const emt_ctx* c) { return c ? (int32_t)c->order.size() : 0; }
 
+int64_t emt_tracks_in_flight(const emt_ctx* c) { return c ? c->live_g + c->live_c : 0; }
+
 emt_status emt_get_table(emt_ctx* c, int32_t m, int32_t p, int32_t q, double* out, int32_t cap, int32_t* n_out)
 {
     if (!c || !out || !n_out) return fail(c, EMT_ERR_INVALID_ARG, "null argument");
@@ -962,6 +988,7 @@ emt_status emt_debug_set_tracks(emt_ctx* c, int32_t n, const double* rec, const 
     const Plan& pl = c->plan;
     r = drain_done(c);  // injected tracks count toward their events again
     if (r != EMT_OK) return r;
+    c->head_fresh = false;
     int cs = (int)(c->it % 3), side = (int)(c->it & 1);
     EMT_CUDA(c, cudaMemsetAsync(c->pool + pl.cnt + sizeof(Counters) * cs, 0, sizeof(Counters), c->stream));
     double* drec = nullptr;

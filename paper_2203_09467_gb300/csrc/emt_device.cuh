@@ -472,6 +472,11 @@ __device__ __forceinline__ void rk4(const Params<R>& p, R kq, const double x[3],
 // skipping it changes no result.
 constexpr double kChordMargin = 1e-6;  // cm
 
+// A step in a field takes at most kMaxSubsteps substeps of h_max (and at
+// most max_field_step); a step shortened this way ends without an
+// interaction: it bounds the work of one step of a looping track.
+constexpr int kMaxSubsteps = 100;
+
 template <typename R>
 __device__ __forceinline__ bool chord_inside(const Params<R>& p, int vol, const double x[3], const double x1[3])
 {

@@ -5,7 +5,9 @@
 // together").  Two schedules over one context (whose track state stays on
 // the device across requests):
 //   continuous : requests that arrive while others are in flight are
-//                admitted as soon as event slots and track slots allow;
+//                admitted as soon as event slots and track slots allow
+//                and fewer than admit_below tracks are in flight (growing
+//                showers need room: a full track store can only defer);
 //                the step loop advances a few iterations between
 //                admissions, and finished events are read back at once.
 //   batch      : one batch at a time: when the device is idle, every
@@ -101,7 +103,8 @@ extern "C" emt_status emt_serve(emt_ctx* ctx, int32_t n_events, const uint64_t* 
         int arrived = next;
         while (arrived < n_events && arrival_s[arrived] / scale <= now) ++arrived;
         const bool idle = emt_events_in_flight(ctx) == 0;
-        if (next < arrived && (opt->mode == EMT_SERVE_CONTINUOUS || idle)) {
+        const bool room = opt->admit_below <= 0 || emt_tracks_in_flight(ctx) < opt->admit_below;
+        if (next < arrived && (idle || (opt->mode == EMT_SERVE_CONTINUOUS && room))) {
             // admit as many arrived requests as fit, halving on capacity errors
             int want = arrived - next;
             while (want > 0) {

@@ -219,6 +219,15 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
             smax = p.max_field_step;
             interact = false;
         }
+        // at most kMaxSubsteps substeps of h_max per step
+        const double Td = (double)t.T;
+        const double pm = sqrt(Td * (Td + 2.0 * kMe));
+        const double hmax = sqrt(8.0 * (pm / (kFieldC * p.bmag)) * p.rk_delta);
+        const double cap = kMaxSubsteps * hmax;
+        if (smax > cap) {
+            smax = cap;
+            interact = false;
+        }
         bool crossed = false;
         s = propagate_field(p, t.type == 1 ? -1 : 1, (double)t.T, t.vol, t.x, t.u, smax, &e, &crossed);
         boundary = crossed;

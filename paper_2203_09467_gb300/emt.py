@@ -64,7 +64,7 @@ class Primaries(ctypes.Structure):
 
 class ServeOptions(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("steps_per_poll", ctypes.c_int32), ("n_bins", ctypes.c_int32),
-                ("time_scale", ctypes.c_double)]
+                ("time_scale", ctypes.c_double), ("admit_below", ctypes.c_int64)]
 
 
 SERVE = {"continuous": 0, "batch": 1}
@@ -97,6 +97,7 @@ _SIGS = {
     "emt_read_all": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_int32]),
     "emt_events_in_flight": (ctypes.c_int32, [ctypes.c_void_p]),
+    "emt_tracks_in_flight": (ctypes.c_int64, [ctypes.c_void_p]),
     "emt_get_table": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "emt_debug_set_tracks": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
@@ -321,7 +322,7 @@ class Context:
         return hist, summary, ids[:n]
 
     def serve(self, event_ids, arrival_s, prim, mode: str = "continuous", steps_per_poll: int = 8,
-              time_scale: float = 1.0):
+              time_scale: float = 1.0, admit_below: int = -1):
         """Replay a request stream (emt_serve).  prim: host primaries grouped
         by event in arrival order.  Returns admit_s, done_s, hist, summary."""
         ids = np.ascontiguousarray(event_ids, np.uint64)
@@ -335,7 +336,9 @@ class Context:
                 "event": np.ascontiguousarray(ev, np.int32)}
         p = Primaries(len(keep["T"]), _ptr(keep["event"]), _ptr(keep["type"]), _ptr(keep["T"]), _ptr(keep["pos"]),
                       _ptr(keep["dir"]))
-        o = ServeOptions(SERVE[mode], int(steps_per_poll), int(self.n_bins), float(time_scale))
+        if admit_below < 0:  # default: a quarter of the track store
+            admit_below = int(self.options.slot_capacity) // 4
+        o = ServeOptions(SERVE[mode], int(steps_per_poll), int(self.n_bins), float(time_scale), int(admit_below))
         admit = np.zeros(n)
         done = np.zeros(n)
         hist = np.zeros((n, self.n_bins))

@@ -163,11 +163,17 @@ def test_rk4_matches_helix(oracle_mod, pitch, T):
     o = make(oracle_mod, s)
     u0 = np.array([pitch, np.sqrt(1 - pitch ** 2), 0.0])
     t = np.array([1, T, 0, 0, 0, *u0, -1, 0], float)
-    t, sec, info = o.step_one(t, 1, 0)
-    L = info[0]
-    assert abs(L - 5.0) < 1e-12 and info[2] == 0
     p = np.sqrt(T * (T + 2 * ME))
     B = 2.0
+    # each step is at most 100 substeps of h_max = sqrt(8 r delta) and at
+    # most max_field_step; follow the helix over several steps to 5 cm
+    hmax = np.sqrt(8 * (p / (2.99792458 * B)) * s.world[12])
+    L = 0.0
+    while L < 5.0 - 1e-9:
+        t, sec, info = o.step_one(t, 1, 0)
+        assert info[2] == 0 and info[3] == 0
+        assert abs(info[0] - min(s.world[15], 100 * hmax)) < 1e-12
+        L += info[0]
     q = -1.0
     # analytic helix about x: omega = q c B / p per unit path
     w = q * 2.99792458 * B / p
