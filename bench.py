@@ -207,7 +207,8 @@ def gpu_arm(args):
         cfg = dict(best)
         tune = {"best": best, "ms_per_candidate": timings}
     else:
-        cfg = {"block_size": args.block, "loop_mode": args.loop, "graph_steps": args.graph_steps}
+        cfg = {"block_size": args.block, "loop_mode": args.loop, "graph_steps": args.graph_steps,
+               "schedule": args.schedule}
     ctx = emt.context_for(setup, device=local, precision=args.precision, slot_capacity=args.slots, max_events=n,
                           **cfg)
     stream = ctx.stream
@@ -348,7 +349,8 @@ def gpu_arm(args):
         "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
         "data": "synthetic",
-        "config": {"workload": desc, "precision": args.precision, "loop": cfg["loop_mode"],
+        "config": {"workload": desc, "precision": args.precision, "schedule": cfg.get("schedule", "fused"),
+                   "loop": cfg["loop_mode"],
                    "graph_steps": cfg["graph_steps"], "block": cfg["block_size"] or 256,
                    "slot_capacity": args.slots, "events_per_gpu": n,
                    "l2": "512 MB buffer written between timed steps; track state >> L2"},
@@ -432,6 +434,8 @@ def main():
     ap.add_argument("--graph-steps", type=int, default=12)
     ap.add_argument("--slots", type=int, default=1 << 25)
     ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--schedule", default="split", choices=["fused", "split"],
+                    help="step schedule when --loop is not auto")
     ap.add_argument("--one-at-a-time", type=int, default=100,
                     help="events of the plain one-event-at-a-time form to time (0: skip)")
     ap.add_argument("--ref-events", type=int, default=1000)

@@ -72,6 +72,14 @@ typedef int32_t emt_status;
 #define EMT_LOOP_PLAIN 0 /* host loop: one kernel launch and one counter read per step */
 #define EMT_LOOP_GRAPH 1 /* CUDA graph of several steps; one counter read per graph */
 
+/* how one step is laid out on the GPU (same results either way):
+ * FUSED: one kernel; interacting tracks are regrouped by model inside each
+ *   block.  SPLIT: a transport kernel queues the interacting tracks in
+ *   device memory and an interaction kernel samples them in full chunks
+ *   sorted by model (needs one more buffer of slot_capacity records). */
+#define EMT_SCHEDULE_FUSED 0
+#define EMT_SCHEDULE_SPLIT 1
+
 typedef struct emt_ctx emt_ctx;
 
 typedef struct emt_options {
@@ -83,6 +91,7 @@ typedef struct emt_options {
     int32_t block_size;    /* threads per block of the step kernel: 128 or 256; 0 = 256 */
     int32_t loop_mode;     /* EMT_LOOP_* */
     int32_t graph_steps;   /* steps per graph launch (EMT_LOOP_GRAPH); multiple of 6 */
+    int32_t schedule;      /* EMT_SCHEDULE_*: how a step's interactions are grouped */
     uint32_t seed;         /* random stream seed */
     void* cuda_stream;     /* cudaStream_t to use, or NULL for a context-owned stream */
     void* device_pool;     /* caller-owned device memory, or NULL: see emt_pool_bytes */

@@ -1,10 +1,12 @@
 """Autotuner of the step-loop launch configuration.
 
-The tunable knobs are the step kernel's block size (128 or 256 threads: a
-larger block regroups more interacting tracks per model, a smaller one
-leaves more blocks per SM) and the step-loop driver (a host loop with one
-counter read per step, or CUDA graphs of 6, 12 or 24 steps with one counter
-read per graph).  Every candidate transports the same batch of events; the
+The tunable knobs are the step schedule (fused: one kernel regrouping the
+interactions inside each block; split: a transport kernel and an
+interaction kernel joined by a queue in device memory), the block size (128
+or 256 threads: a larger block regroups more interacting tracks per model, a
+smaller one leaves more blocks per SM) and the step-loop driver (a host loop
+with one counter read per step, or CUDA graphs of 12 or 24 steps with one
+counter read per graph).  Every candidate transports the same batch of events; the
 fastest by CUDA-event time wins.  Results are cached per GPU name, workload
 name and precision in a JSON file next to this module.
 """
@@ -20,9 +22,10 @@ from . import emt
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_autotune_cache.json")
 
 CANDIDATES = [
-    {"block_size": b, "loop_mode": loop, "graph_steps": k}
+    {"block_size": b, "loop_mode": loop, "graph_steps": k, "schedule": sched}
+    for sched in ("fused", "split")
     for b in (128, 256)
-    for loop, k in (("plain", 12), ("graph", 6), ("graph", 12), ("graph", 24))
+    for loop, k in (("plain", 12), ("graph", 12), ("graph", 24))
 ]
 
 

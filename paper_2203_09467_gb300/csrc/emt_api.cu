@@ -42,9 +42,11 @@ struct Plan {
     size_t zb, lmat, lbin;
     size_t st_ev, st_type, st_T, st_pos, st_dir, st_uid, st_slot, st_ids, st_start, st_runs;
     size_t slots_tmp, out_hist, out_summary;
+    size_t iq[13];  // split schedule: interaction queue fields
     int64_t Q;
     int max_events, hstride, max_prim;
     bool mixed;
+    bool split;
 };
 
 Plan make_plan(const emt_options& o)
@@ -95,6 +97,14 @@ Plan make_plan(const emt_options& o)
     p.st_start = p.add(E * 4);
     p.st_runs = p.add(E * 4);
     p.slots_tmp = p.add(E * 4);
+    p.split = o.schedule == EMT_SCHEDULE_SPLIT;
+    if (p.split) {
+        // x y z ux uy uz T uid dep ev step tv src
+        const size_t iqs[13] = {8, 8, 8, rs, rs, rs, rs, 8, 8, 4, 4, 4, 4};
+        for (int f = 0; f < 13; ++f) p.iq[f] = p.add(Q * iqs[f]);
+    } else {
+        for (int f = 0; f < 13; ++f) p.iq[f] = 0;
+    }
     p.out_hist = p.add(E * (size_t)o.max_bins * sizeof(double));
     p.out_summary = p.add(E * EMT_SUMMARY_LEN * sizeof(double));
     return p;
@@ -109,6 +119,7 @@ bool valid_options(const emt_options& o, std::string& why)
     if (o.block_size != 0 && o.block_size != 128 && o.block_size != 256)
         return why = "block_size must be 0 (default), 128 or 256", false;
     if (o.loop_mode != EMT_LOOP_PLAIN && o.loop_mode != EMT_LOOP_GRAPH) return why = "loop_mode", false;
+    if (o.schedule != EMT_SCHEDULE_FUSED && o.schedule != EMT_SCHEDULE_SPLIT) return why = "schedule", false;
     if (o.loop_mode == EMT_LOOP_GRAPH && (o.graph_steps <= 0 || o.graph_steps % 6 != 0))
         return why = "graph_steps must be a positive multiple of 6", false;
     return true;
@@ -132,6 +143,7 @@ struct emt_ctx {
     int64_t it = 0;  // step-loop iterations so far
     int64_t live_g = 0, live_c = 0;
     int resident_blocks = 0;
+    int resident_a = 0, resident_b = 0;  // split schedule: transport, interaction kernels
     int block = 128;
     // host event table
     std::vector<uint64_t> slot_id;
@@ -207,6 +219,22 @@ void fill_common(emt_ctx* c, Params<R>& p)
 {
     const Plan& pl = c->plan;
     fill_tracks(c, p);
+    if (pl.split) {
+        InterQueue<R>& q = p.iq;
+        q.x = c->at<double>(pl.iq[0]);
+        q.y = c->at<double>(pl.iq[1]);
+        q.z = c->at<double>(pl.iq[2]);
+        q.ux = c->at<R>(pl.iq[3]);
+        q.uy = c->at<R>(pl.iq[4]);
+        q.uz = c->at<R>(pl.iq[5]);
+        q.T = c->at<R>(pl.iq[6]);
+        q.uid = c->at<uint64_t>(pl.iq[7]);
+        q.dep = c->at<double>(pl.iq[8]);
+        q.ev = c->at<uint32_t>(pl.iq[9]);
+        q.step = c->at<uint32_t>(pl.iq[10]);
+        q.tv = c->at<uint32_t>(pl.iq[11]);
+        q.src = c->at<uint32_t>(pl.iq[12]);
+    }
     p.Q = pl.Q;
     p.cnt = c->at<Counters>(pl.cnt);
     p.status = c->at<int>(pl.status);
@@ -380,10 +408,15 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
         int64_t chunks = (c->live_g + c->block - 1) / c->block + (c->live_c + c->block - 1) / c->block;
         int grid = (int)std::max<int64_t>(1, std::min<int64_t>(chunks, c->resident_blocks));
         EMT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
-        cudaError_t e = Launch<R>::step(p, side, cin, cout, cclr, grid, c->block, c->stream);
+        cudaError_t e =
+            c->plan.split
+                ? Launch<R>::step_split(p, side, cin, cout, cclr,
+                                        (int)std::max<int64_t>(1, std::min<int64_t>(chunks, c->resident_a)),
+                                        c->resident_b, c->block, c->stream)
+                : Launch<R>::step(p, side, cin, cout, cclr, grid, c->block, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
         EMT_CUDA(c, cudaEventRecord(c->ev1, c->stream));
-        s.kernel_launches += 1;
+        s.kernel_launches += c->plan.split ? 2 : 1;
         c->it += 1;
         s.iterations += 1;
         return read_counts();
@@ -410,7 +443,10 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
                 EMT_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
                 for (int k = 0; k < K; ++k) {
                     int side = k & 1, cin = k % 3, cout = (k + 1) % 3, cclr = (k + 2) % 3;
-                    cudaError_t e = Launch<R>::step(p, side, cin, cout, cclr, c->resident_blocks, c->block, c->stream);
+                    cudaError_t e = c->plan.split ? Launch<R>::step_split(p, side, cin, cout, cclr, c->resident_a,
+                                                                          c->resident_b, c->block, c->stream)
+                                                  : Launch<R>::step(p, side, cin, cout, cclr, c->resident_blocks,
+                                                                    c->block, c->stream);
                     if (e != cudaSuccess) {
                         cudaStreamEndCapture(c->stream, &g);
                         return cuda_fail(c, e, "graph capture");
@@ -423,7 +459,7 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
             EMT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
             EMT_CUDA(c, cudaGraphLaunch(c->graph, c->stream));
             EMT_CUDA(c, cudaEventRecord(c->ev1, c->stream));
-            s.kernel_launches += K;
+            s.kernel_launches += c->plan.split ? 2 * K : K;
             c->it += K;
             s.iterations += K;
             done_it += K;
@@ -519,6 +555,7 @@ void emt_default_options(emt_options* o)
     o->block_size = 0;
     o->loop_mode = EMT_LOOP_PLAIN;
     o->graph_steps = 12;
+    o->schedule = EMT_SCHEDULE_FUSED;
     o->seed = 1;
 }
 
@@ -578,6 +615,14 @@ emt_status emt_create(const emt_options* o, emt_ctx** out)
     cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, o->device);
     int per_sm = c->mixed() ? Launch<float>::max_blocks_per_sm(c->block) : Launch<double>::max_blocks_per_sm(c->block);
     c->resident_blocks = std::max(1, dev_sms * per_sm);
+    if (c->plan.split) {
+        auto blocks = [&](int which) {
+            return c->mixed() ? Launch<float>::max_blocks_split(c->block, which)
+                              : Launch<double>::max_blocks_split(c->block, which);
+        };
+        c->resident_a = std::max(1, dev_sms * blocks(0));
+        c->resident_b = std::max(1, dev_sms * blocks(1));
+    }
     c->slot_id.assign(pl.max_events, 0);
     c->slot_state.assign(pl.max_events, 0);
     c->free_slots.reserve(pl.max_events);

@@ -72,6 +72,28 @@ struct Counters {
     int n[2];      // photons, charged
     int work;      // chunk dispenser
     int used;      // growth tokens taken (steps with two outputs)
+    int n_int;     // split schedule: tracks queued for an interaction
+    int work_b;    // split schedule: chunk dispenser of the interaction kernel
+    int pad[2];
+};
+
+// Split schedule: tracks that interact in a step, queued by the transport
+// kernel for the interaction kernel (structure of arrays, Q entries).
+template <typename R>
+struct InterQueue {
+    double* x;
+    double* y;
+    double* z;
+    R* ux;
+    R* uy;
+    R* uz;
+    R* T;
+    uint64_t* uid;
+    double* dep;     // energy deposited by the transport part of the step
+    uint32_t* ev;
+    uint32_t* step;
+    uint32_t* tv;    // type | (volume + 2) << 8 | model << 24
+    uint32_t* src;   // index of the track in the input buffer (for deferral)
 };
 
 template <typename R>
@@ -116,6 +138,7 @@ struct Params {
     long long Q;
     Counters* cnt;  // [3]
     int* status;
+    InterQueue<R> iq;  // split schedule only
 };
 
 __device__ __forceinline__ uint32_t pack_tv(int type, int vol) { return (uint32_t)type | ((uint32_t)(vol + 2) << 8); }

@@ -42,6 +42,10 @@ struct Launch {
     static cudaError_t get_tracks(const Params<R>& p, int side, int nG, int nC, double* rec, uint64_t* uid,
                                   int32_t* slot, cudaStream_t st);
     static int max_blocks_per_sm(int block);
+    // split schedule: transport kernel then interaction kernel
+    static cudaError_t step_split(const Params<R>& p, int side, int cin, int cout, int cclr, int grid_a, int grid_b,
+                                  int block, cudaStream_t st);
+    static int max_blocks_split(int block, int which);
 };
 
 }  // namespace emt

@@ -60,3 +60,40 @@ int Launch<R>::max_blocks_per_sm(int block)
 }
 
 }  // namespace emt
+
+#include "emt_split.cuh"
+
+namespace emt {
+
+template <typename R>
+cudaError_t Launch<R>::step_split(const Params<R>& p, int side, int cin, int cout, int cclr, int grid_a, int grid_b,
+                                  int block, cudaStream_t st)
+{
+    if (block == 128) {
+        k_transport<R, 128><<<grid_a, 128, 0, st>>>(p, side, cin, cout, cclr);
+        k_interact<R, 128><<<grid_b, 128, 0, st>>>(p, side, cin, cout);
+    } else if (block == 256) {
+        k_transport<R, 256><<<grid_a, 256, 0, st>>>(p, side, cin, cout, cclr);
+        k_interact<R, 256><<<grid_b, 256, 0, st>>>(p, side, cin, cout);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename R>
+int Launch<R>::max_blocks_split(int block, int which)
+{
+    int n = 0;
+    cudaError_t e;
+    if (which == 0)
+        e = block == 128 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_transport<R, 128>, 128, 0)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_transport<R, 256>, 256, 0);
+    else
+        e = block == 128 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_interact<R, 128>, 128, 0)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_interact<R, 256>, 256, 0);
+    if (e != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
+}  // namespace emt

@@ -1,0 +1,220 @@
+// emt_split.cuh -- the split schedule of one step: a transport kernel and
+// an interaction kernel per step-loop iteration.
+//
+// The fused kernel (emt_step.cuh) regroups the interacting tracks of each
+// chunk inside its block, which leaves most warps of the block waiting at
+// a barrier while a few run the samplers.  Here the transport kernel runs
+// phase A for every track and appends the tracks that interact to a global
+// queue (warp-aggregated, one atomic per warp); the interaction kernel then
+// takes the queue in full chunks, counting-sorts each chunk by model in
+// shared memory and samples with every lane busy.  The cost is one more
+// write and read of the interacting tracks' state (a few percent of the
+// step's track-state traffic); the results are the same as the fused
+// schedule's (same arithmetic, same random streams).
+#pragma once
+
+#include "emt_step.cuh"
+
+namespace emt {
+
+__device__ __forceinline__ uint32_t pack_tvm(int type, int vol, int model)
+{
+    return (uint32_t)type | ((uint32_t)(vol + 2) << 8) | ((uint32_t)model << 24);
+}
+
+template <typename R, int BS>
+__global__ void __launch_bounds__(BS, 512 / BS) k_transport(Params<R> p, int side, int cin, int cout, int cclr)
+{
+    __shared__ int s_chunk;
+    if (blockIdx.x == 0 && threadIdx.x == 0) p.cnt[cclr] = Counters{};
+    const Tracks<R> qi = p.q[side];
+    const Tracks<R> qo = p.q[side ^ 1];
+    const int nG = p.cnt[cin].n[0];
+    const int nC = p.cnt[cin].n[1];
+    const long long Q = p.Q;
+    const int chunksG = (nG + BS - 1) / BS;
+    const int chunksC = (nC + BS - 1) / BS;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const unsigned lanes_below = (1u << lane) - 1u;
+    Counters* const co = &p.cnt[cout];
+    const InterQueue<R> iq = p.iq;
+
+    for (;;) {
+        if (tid == 0) s_chunk = atomicAdd(&p.cnt[cin].work, 1);
+        __syncthreads();
+        const int chunk = s_chunk;
+        __syncthreads();
+        if (chunk >= chunksG + chunksC) break;
+        const bool photon_chunk = chunk < chunksG;
+        const long long i = photon_chunk ? (long long)chunk * BS + tid : (long long)(chunk - chunksG) * BS + tid;
+        const long long n_here = photon_chunk ? nG : nC;
+        const bool active = i < n_here;
+        const long long src = photon_chunk ? i : Q - nC + i;
+
+        TrackReg<R> t;
+        Effects fx;
+        StepOut<R> o;
+        o.n = 0;
+        int model = kNoInteraction;
+        if (active) {
+            load_track(qi, src, t);
+            bool alive;
+            model = transport_part(p, t, fx, alive);
+            if (model == kNoInteraction) {
+                finish_step(p, t, alive, fx, o);
+                apply_effects(p, t.ev, t.step, fx);
+            }
+        }
+        {
+            const unsigned ms = __ballot_sync(0xFFFFFFFFu, active);
+            if (lane == 0 && ms) atomicAdd(&p.total_steps[0], (unsigned long long)__popc(ms));
+        }
+        emit(p, qo, co, lane, o, t.x, t.ev, t.vol);
+        // queue the interacting tracks
+        const bool need = model != kNoInteraction;
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, need);
+        if (m) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&p.cnt[cin].n_int, __popc(m));
+            base = __shfl_sync(0xFFFFFFFFu, base, 0);
+            if (need) {
+                const long long k = (long long)base + __popc(m & lanes_below);
+                if (k < Q) {
+                    iq.x[k] = t.x[0];
+                    iq.y[k] = t.x[1];
+                    iq.z[k] = t.x[2];
+                    iq.ux[k] = t.u[0];
+                    iq.uy[k] = t.u[1];
+                    iq.uz[k] = t.u[2];
+                    iq.T[k] = t.T;
+                    iq.uid[k] = t.uid;
+                    iq.dep[k] = fx.dep;
+                    iq.ev[k] = t.ev;
+                    iq.step[k] = t.step;
+                    iq.tv[k] = pack_tvm(t.type, t.vol, model);
+                    iq.src[k] = (uint32_t)src;
+                } else {
+                    atomicOr(p.status, kStatusQueueOverflow);
+                }
+            }
+        }
+    }
+}
+
+template <typename R, int BS>
+__global__ void __launch_bounds__(BS, 512 / BS) k_interact(Params<R> p, int side, int cin, int cout)
+{
+    __shared__ int s_chunk;
+    __shared__ int count[kNumModels];
+    __shared__ int offset[kNumModels + 1];
+    __shared__ unsigned short perm[BS];
+    const Tracks<R> qi = p.q[side];
+    const Tracks<R> qo = p.q[side ^ 1];
+    const long long Q = p.Q;
+    const long long ntot = (long long)p.cnt[cin].n[0] + p.cnt[cin].n[1];
+    const long long spare = Q - ntot;
+    const bool unlimited = 2 * ntot <= Q;
+    const int n_int = p.cnt[cin].n_int;
+    const int chunks = (n_int + BS - 1) / BS;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const unsigned lanes_below = (1u << lane) - 1u;
+    Counters* const co = &p.cnt[cout];
+    const InterQueue<R> iq = p.iq;
+
+    for (;;) {
+        if (tid == 0) s_chunk = atomicAdd(&p.cnt[cin].work_b, 1);
+        if (tid < kNumModels) count[tid] = 0;
+        __syncthreads();
+        const int chunk = s_chunk;
+        if (chunk >= chunks) break;
+        const long long r0 = (long long)chunk * BS;
+        const int n_here = (int)(n_int - r0 < BS ? n_int - r0 : BS);
+        // counting sort of the chunk's records by model
+        int model = -1, rank = 0;
+        if (tid < n_here) {
+            model = (int)(iq.tv[r0 + tid] >> 24);
+            rank = atomicAdd(&count[model], 1);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int acc = 0;
+            for (int k = 0; k < kNumModels; ++k) {
+                offset[k] = acc;
+                acc += count[k];
+            }
+            offset[kNumModels] = acc;
+        }
+        __syncthreads();
+        if (model >= 0) perm[offset[model] + rank] = (unsigned short)tid;
+        __syncthreads();
+
+        const bool mine = tid < n_here;
+        TrackReg<R> t;
+        Effects fx;
+        StepOut<R> o;
+        o.n = 0;
+        bool stepped = false;
+        long long rsrc = 0;
+        if (mine) {
+            const long long r = r0 + perm[tid];
+            const uint32_t tv = iq.tv[r];
+            t.x[0] = iq.x[r];
+            t.x[1] = iq.y[r];
+            t.x[2] = iq.z[r];
+            t.u[0] = iq.ux[r];
+            t.u[1] = iq.uy[r];
+            t.u[2] = iq.uz[r];
+            t.T = iq.T[r];
+            t.uid = iq.uid[r];
+            t.ev = iq.ev[r];
+            t.step = iq.step[r];
+            t.type = (int)(tv & 0xFFu);
+            t.vol = (int)((tv >> 8) & 0xFFFFu) - 2;
+            rsrc = iq.src[r];
+            fx.dep = iq.dep[r];
+            fx.esc = 0.0;
+            fx.kill = 0.0;
+            fx.vol = t.vol;
+            fx.finished = false;
+            fx.live_delta = 0;
+            interaction_part(p, t, (int)(tv >> 24), fx, o);
+            stepped = true;
+        }
+        if (!unlimited) {
+            const bool need = stepped && o.n == 2;
+            const unsigned m = __ballot_sync(0xFFFFFFFFu, need);
+            if (m) {
+                const int k = __popc(m);
+                const int leader = __ffs(m) - 1;
+                int got = 0;
+                if (lane == leader) {
+                    int old = atomicAdd(&p.cnt[cin].used, k);
+                    long long avail = spare - old;
+                    got = avail <= 0 ? 0 : (avail >= k ? k : (int)avail);
+                    if (got < k) atomicSub(&p.cnt[cin].used, k - got);
+                }
+                got = __shfl_sync(0xFFFFFFFFu, got, leader);
+                if (need && __popc(m & lanes_below) >= got) {
+                    // no room for the second output: discard the whole step
+                    load_track(qi, rsrc, t);
+                    copy_out(t, o);
+                    stepped = false;
+                }
+            }
+        }
+        if (stepped) apply_effects(p, t.ev, t.step, fx);
+        {
+            const unsigned md = __ballot_sync(0xFFFFFFFFu, mine && !stepped);
+            if (lane == 0 && md) {
+                atomicAdd(&p.total_steps[0], -(unsigned long long)__popc(md));
+                atomicAdd(&p.total_steps[1], (unsigned long long)__popc(md));
+            }
+        }
+        emit(p, qo, co, lane, o, t.x, t.ev, t.vol);
+        __syncthreads();
+    }
+}
+
+}  // namespace emt

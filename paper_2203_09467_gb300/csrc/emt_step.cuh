@@ -513,10 +513,7 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_step(Params<R> p, int side, in
     __shared__ int s_chunk;
     __shared__ Staging<R, BS> sg;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        p.cnt[cclr].n[0] = 0;
-        p.cnt[cclr].n[1] = 0;
-        p.cnt[cclr].work = 0;
-        p.cnt[cclr].used = 0;
+        p.cnt[cclr] = Counters{};
     }
     const Tracks<R> qi = p.q[side];
     const Tracks<R> qo = p.q[side ^ 1];

@@ -17,6 +17,7 @@ from . import build as _build
 HOST, DEVICE = 0, 1
 PRECISION = {"fp64": 0, "mixed": 1}
 LOOP = {"plain": 0, "graph": 1}
+SCHEDULE = {"fused": 0, "split": 1}
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "CAPACITY", -3: "CUDA", -4: "BAD_STATE", -5: "TIMEOUT",
           -6: "NOT_READY", -7: "HOST_OOM"}
 SUMMARY_FIELDS = ("edep", "escaped", "killed", "e_in", "n_steps", "n_tracks")
@@ -31,7 +32,8 @@ class EmtError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("precision", ctypes.c_int32), ("slot_capacity", ctypes.c_int64),
                 ("max_events", ctypes.c_int32), ("max_bins", ctypes.c_int32), ("block_size", ctypes.c_int32),
-                ("loop_mode", ctypes.c_int32), ("graph_steps", ctypes.c_int32), ("seed", ctypes.c_uint32),
+                ("loop_mode", ctypes.c_int32), ("graph_steps", ctypes.c_int32), ("schedule", ctypes.c_int32),
+                ("seed", ctypes.c_uint32),
                 ("cuda_stream", ctypes.c_void_p), ("device_pool", ctypes.c_void_p), ("pool_bytes", ctypes.c_size_t)]
 
 
@@ -182,7 +184,7 @@ class Context:
 
     def __init__(self, *, device: int = 0, precision: str = "fp64", slot_capacity: int = 1 << 22,
                  max_events: int = 10000, max_bins: int = 128, block_size: int = 0, loop_mode: str = "plain",
-                 graph_steps: int = 12, seed: int = 1, use_torch_pool: bool = True):
+                 graph_steps: int = 12, seed: int = 1, use_torch_pool: bool = True, schedule: str = "fused"):
         import torch
         L = lib()
         self._torch = torch
@@ -196,6 +198,7 @@ class Context:
         o.block_size = int(block_size)
         o.loop_mode = LOOP[loop_mode]
         o.graph_steps = int(graph_steps)
+        o.schedule = SCHEDULE[schedule]
         o.seed = int(seed) & 0xFFFFFFFF
         self.device = torch.device("cuda", device)
         self.stream = torch.cuda.Stream(device=self.device)

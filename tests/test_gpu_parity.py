@@ -275,6 +275,21 @@ def test_capacity_deferral_does_not_change_results(emt):
     assert np.allclose(h1, h2, rtol=1e-12, atol=1e-12)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_split_schedule_matches_fused(emt, precision):
+    s = W.calo_field_setup()
+    prim = _calo_mix(seed=15)
+    n = 40
+    h1, s1, st1 = gpu_run(emt, s, prim, n, precision=precision, schedule="fused")
+    h2, s2, st2 = gpu_run(emt, s, prim, n, precision=precision, schedule="split", loop_mode="graph")
+    assert np.array_equal(s1[:, 4:], s2[:, 4:])
+    assert np.allclose(s1[:, :4], s2[:, :4], rtol=1e-12, atol=0)
+    h3, s3, st3 = gpu_run(emt, s, prim, n, precision=precision, schedule="split", slot_capacity=4000)
+    assert st3["deferred"] > 0
+    assert np.array_equal(s1[:, 4:], s3[:, 4:])
+    assert np.allclose(s1[:, :4], s3[:, :4], rtol=1e-12, atol=0)
+
+
 def test_graph_loop_matches_plain_loop(emt):
     s = W.calo_setup()
     prim = _calo_mix(seed=12)
