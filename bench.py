@@ -300,13 +300,14 @@ def gpu_arm(args):
     # roofline of the step kernel
     peaks, src = load_peaks()
     kern_ms = sum(s["kernel_ms"] for s in stats)
-    kern_launch = sum(s["kernel_launches"] for s in stats)
+    kern_launch = sum(s["iterations"] for s in stats)  # one step-loop iteration = one step (1 or 2 kernels)
     state_bytes = sum(s["state_bytes"] for s in stats)
     achieved = state_bytes / (kern_ms / 1e3) / 1e9
     peak = float(peaks.get("hbm_gbs", 6800.0))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": None, "peak_source": f"{src} hbm_gbs",
-            "kernel": "k_step", "launches": kern_launch, "mean_launch_ms": kern_ms / max(kern_launch, 1),
+            "kernel": ("step = k_transport + k_interact" if cfg.get("schedule") == "split" else "k_step"),
+            "launches": kern_launch, "mean_launch_ms": kern_ms / max(kern_launch, 1),
             "algorithmic_bytes_per_launch": state_bytes / max(kern_launch, 1),
             "kernel_share_of_step": kern_ms / total_ms}
     if args.traffic_per_launch:

@@ -367,37 +367,55 @@ __device__ __forceinline__ Exit nav_exit(const Params<R>& p, int vol, const doub
     e.axis = -1;
     e.plane = 0.0;
     if (vol >= 0) {
+        // Candidates: the z plane ahead, then the x and y walls ahead; the
+        // exit is the smallest (pl - x)/d, ties to the earlier candidate.
+        // FP32 estimates of the three quotients (relative error < 1e-6)
+        // select the candidates that can be the minimum (within 1e-5 of the
+        // smallest estimate); only those are divided in FP64, in the same
+        // order and with the same strict comparison, so the result is the
+        // one all three FP64 divisions would give.
         const int L = p.n_layers;
+        double pl[3], diff[3];
+        int nx[3];
+        bool has[3];
+        float tf[3];
+        has[2] = d[2] != 0.0;
         if (d[2] > 0.0) {
-            double pl = p.zb[vol + 1];
-            double t = (pl - x[2]) / d[2];
-            if (t < e.t) {
-                e.t = t;
-                e.next = vol + 1 < L ? vol + 1 : kVolWorld;
-                e.axis = 2;
-                e.plane = pl;
-            }
-        } else if (d[2] < 0.0) {
-            double pl = p.zb[vol];
-            double t = (pl - x[2]) / d[2];
-            if (t < e.t) {
-                e.t = t;
-                e.next = vol > 0 ? vol - 1 : kVolWorld;
-                e.axis = 2;
-                e.plane = pl;
-            }
+            pl[2] = p.zb[vol + 1];
+            nx[2] = vol + 1 < L ? vol + 1 : kVolWorld;
+        } else {
+            pl[2] = p.zb[vol];
+            nx[2] = vol > 0 ? vol - 1 : kVolWorld;
         }
-        const double half[2] = {p.hx, p.hy};
+        has[0] = d[0] != 0.0;
+        pl[0] = d[0] > 0.0 ? p.hx : -p.hx;
+        nx[0] = kVolWorld;
+        has[1] = d[1] != 0.0;
+        pl[1] = d[1] > 0.0 ? p.hy : -p.hy;
+        nx[1] = kVolWorld;
+        float tmin = __int_as_float(0x7F800000);
 #pragma unroll
-        for (int a = 0; a < 2; ++a) {
-            if (d[a] == 0.0) continue;
-            double pl = d[a] > 0.0 ? half[a] : -half[a];
-            double t = (pl - x[a]) / d[a];
+        for (int a = 0; a < 3; ++a) {
+            if (!has[a]) continue;
+            diff[a] = pl[a] - x[a];
+            tf[a] = (float)diff[a] / (float)d[a];
+            tmin = fminf(tmin, tf[a]);
+        }
+        // a non-finite smallest estimate (a direction component below the
+        // FP32 range) falls back to dividing every candidate
+        const float thr = (tmin > -1e30f && tmin < 1e30f) ? tmin + fabsf(tmin) * 1e-5f + 1e-30f
+                                                          : __int_as_float(0x7F800000);
+        const int order[3] = {2, 0, 1};
+#pragma unroll
+        for (int oi = 0; oi < 3; ++oi) {
+            const int a = order[oi];
+            if (!has[a] || !(tf[a] <= thr)) continue;
+            double t = diff[a] / d[a];
             if (t < e.t) {
                 e.t = t;
-                e.next = kVolWorld;
+                e.next = nx[a];
                 e.axis = a;
-                e.plane = pl;
+                e.plane = pl[a];
             }
         }
     } else {
