@@ -59,6 +59,37 @@ def test_mixed_matches_oracle_statistically(emt, oracle_mod, workload):
     assert abs(sm[:, 4].mean() / so[:, 4].mean() - 1) < 0.03
 
 
+def test_mixed_error_statement(emt, oracle_mod):
+    """The mixed path's error against the FP64 oracle, per result, on 4,000
+    events of 10 GeV electrons in the calorimeter (independent samples):
+    total deposition (difference of means and its standard error), the
+    sampling fraction in LAr, the per-layer profile (Hotelling T^2) and the
+    worst per-event energy ledger.  Printed for the record; the asserts are
+    the statistical bars of the test above."""
+    from stats_util import mean_test
+    s = W.calo_setup()
+    n = 4000
+    prim = W.calo_primaries(n)
+    hm, sm, _ = run(emt, s, prim, n, "mixed")
+    o = oracle_mod.Oracle(s.materials, s.physics, s.layers, s.world, s.seed)
+    ho, so = o.run(prim, n, np.arange(n))
+    d, se = mean_test(sm[:, 0], so[:, 0])
+    fm = hm[:, 1::2].sum(1) / hm.sum(1)
+    fo = ho[:, 1::2].sum(1) / ho.sum(1)
+    dfr, sefr = mean_test(fm, fo)
+    t2, dof, p = profile_test(hm, ho)
+    led = np.abs(sm[:, 3] - sm[:, 0] - sm[:, 1] - sm[:, 2]) / sm[:, 3]
+    print(f"\nmixed vs FP64 oracle, {n} x 10 GeV e-: total deposition {sm[:, 0].mean():.3f} vs "
+          f"{so[:, 0].mean():.3f} MeV, difference {d:+.3f} +- {se:.3f} MeV ({d / se:+.2f} sigma); "
+          f"LAr sampling fraction {fm.mean():.5f} vs {fo.mean():.5f} ({dfr / sefr:+.2f} sigma); "
+          f"profile T2 = {t2:.1f} on {dof} groups, p = {p:.3f}; worst ledger {led.max():.2e}; "
+          f"steps/event {sm[:, 4].mean():.0f} vs {so[:, 4].mean():.0f}")
+    assert abs(d) < 4 * se + 1e-6 * so[:, 0].mean()
+    assert abs(dfr) < 4 * sefr
+    assert p > 1e-3
+    assert led.max() < 1e-5
+
+
 def test_mixed_is_deterministic(emt):
     s = W.calo_setup()
     prim = W.calo_primaries(200, energy=3000.0)
