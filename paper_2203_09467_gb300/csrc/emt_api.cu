@@ -702,6 +702,7 @@ emt_status emt_load_materials(emt_ctx* c, const emt_material* mats, int32_t n, c
     for (int k = 0; k < 3; ++k) {
         c->pd.cut[k] = ph->cut_MeV[k];
         c->pf.cut[k] = ph->cut_MeV[k];
+        c->pd.cutf[k] = c->pf.cutf[k] = (float)ph->cut_MeV[k];
     }
     c->pd.grid = b.grid;
     c->pd.tab = b.tab;
@@ -712,6 +713,8 @@ emt_status emt_load_materials(emt_ctx* c, const emt_material* mats, int32_t n, c
     c->pd.log10_lo = c->pf.log10_lo = l10;
     c->pd.step_frac = c->pf.step_frac = ph->step_frac;
     c->pd.final_range = c->pf.final_range = ph->final_range_cm;
+    c->pd.step_fracf = c->pf.step_fracf = (float)ph->step_frac;
+    c->pd.final_rangef = c->pf.final_rangef = (float)ph->final_range_cm;
     drop_graph(c);
     c->have_materials = true;
     return EMT_OK;
@@ -1214,7 +1217,10 @@ extern "C" emt_status emt_transport_static(int32_t device, uint32_t seed, const 
     b.tabf = nullptr;
     b.gridf = nullptr;
     if (build_tables(b, reinterpret_cast<double*>(pool + pl.scratch), st) != cudaSuccess) return EMT_ERR_CUDA;
-    for (int k = 0; k < 3; ++k) p.cut[k] = ph->cut_MeV[k];
+    for (int k = 0; k < 3; ++k) {
+        p.cut[k] = ph->cut_MeV[k];
+        p.cutf[k] = (float)ph->cut_MeV[k];
+    }
     p.grid = b.grid;
     p.tab = b.tab;
     p.n_grid = n_grid;
@@ -1222,6 +1228,8 @@ extern "C" emt_status emt_transport_static(int32_t device, uint32_t seed, const 
     p.log10_lo = (float)std::log10(ph->grid_lo_MeV);
     p.step_frac = ph->step_frac;
     p.final_range = ph->final_range_cm;
+    p.step_fracf = (float)ph->step_frac;
+    p.final_rangef = (float)ph->final_range_cm;
 
     // ---- geometry
     double zb[kMaxLayers + 1];

@@ -49,6 +49,36 @@ __device__ __forceinline__ float mcos(float x) { return cosf(x); }
 __device__ __forceinline__ double mfmax(double a, double b) { return fmax(a, b); }
 __device__ __forceinline__ float mfmax(float a, float b) { return fmaxf(a, b); }
 
+// ------------------------------------------------------------------ conversions
+// Measured on GB300: exact conversions between the physics type and FP64
+// are fastest as the hardware instructions, but an FP32 estimate of a
+// double (bin search, navigation prefilter) is cheaper from integer
+// operations on the bit pattern than from a rounding conversion.
+
+// double -> float truncated toward zero, for estimates only (relative error
+// < 2^-23; magnitudes below the float range give 0, above it infinity)
+__device__ __forceinline__ float d2f_est(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned sign = (unsigned)(b >> 63) << 31;
+    const int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;
+    if (e <= 0) return __uint_as_float(sign);
+    if (e >= 255) return __uint_as_float(sign | 0x7F800000u);
+    return __uint_as_float(sign | ((unsigned)e << 23) | (unsigned)((b >> 29) & 0x7FFFFFu));
+}
+
+// the physics type R to and from FP64 (identity for the FP64 path)
+__device__ __forceinline__ double to_d(double x) { return x; }
+__device__ __forceinline__ double to_d(float x) { return (double)x; }
+template <typename R>
+__device__ __forceinline__ R from_d(double x);
+template <>
+__device__ __forceinline__ double from_d<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float from_d<float>(double x) { return (float)x; }
+__device__ __forceinline__ float est_f(double x) { return d2f_est(x); }
+__device__ __forceinline__ float est_f(float x) { return x; }
+
 // ------------------------------------------------------------------ layout
 // One ping-pong side of the track store, structure of arrays.  Photons
 // occupy [0, nG) from the front, charged tracks [Q-nC, Q) from the back.
@@ -108,6 +138,8 @@ struct Params {
     const int* vacuum;
     double cut[3];
     double step_frac, final_range;
+    float cutf[3];  // the same in FP32 (mixed path)
+    float step_fracf, final_rangef;
     // geometry
     const double* zb;
     const int* lmat;
@@ -140,6 +172,32 @@ struct Params {
     int* status;
     InterQueue<R> iq;  // split schedule only
 };
+
+// production cut of particle type t and the e+- step-limit constants in R
+template <typename R>
+__device__ __forceinline__ R pcut(const Params<R>& p, int t)
+{
+    if constexpr (sizeof(R) == 8)
+        return p.cut[t];
+    else
+        return p.cutf[t];
+}
+template <typename R>
+__device__ __forceinline__ R pstep_frac(const Params<R>& p)
+{
+    if constexpr (sizeof(R) == 8)
+        return p.step_frac;
+    else
+        return p.step_fracf;
+}
+template <typename R>
+__device__ __forceinline__ R pfinal_range(const Params<R>& p)
+{
+    if constexpr (sizeof(R) == 8)
+        return p.final_range;
+    else
+        return p.final_rangef;
+}
 
 __device__ __forceinline__ uint32_t pack_tv(int type, int vol) { return (uint32_t)type | ((uint32_t)(vol + 2) << 8); }
 __device__ __forceinline__ int tv_type(uint32_t tv) { return (int)(tv & 0xFFu); }
@@ -256,7 +314,7 @@ __device__ __forceinline__ bool le_pos(float a, float b) { return __float_as_int
 template <typename R>
 __device__ __forceinline__ int find_bin(const Params<R>& p, R E)
 {
-    float g = ((float)p.bpd) * (log10f((float)E) - p.log10_lo);
+    float g = ((float)p.bpd) * (log10f(est_f(E)) - p.log10_lo);
     int n = (int)g;
     int top = p.n_grid - 2;
     n = n < 0 ? 0 : (n > top ? top : n);
@@ -369,7 +427,8 @@ __device__ __forceinline__ Exit nav_exit(const Params<R>& p, int vol, const doub
     if (vol >= 0) {
         // Candidates: the z plane ahead, then the x and y walls ahead; the
         // exit is the smallest (pl - x)/d, ties to the earlier candidate.
-        // FP32 estimates of the three quotients (relative error < 1e-6)
+        // FP32 estimates of the three quotients (operands truncated to FP32
+        // by integer operations, quotient relative error < 1e-6)
         // select the candidates that can be the minimum (within 1e-5 of the
         // smallest estimate); only those are divided in FP64, in the same
         // order and with the same strict comparison, so the result is the
@@ -398,7 +457,7 @@ __device__ __forceinline__ Exit nav_exit(const Params<R>& p, int vol, const doub
         for (int a = 0; a < 3; ++a) {
             if (!has[a]) continue;
             diff[a] = pl[a] - x[a];
-            tf[a] = (float)diff[a] / (float)d[a];
+            tf[a] = d2f_est(diff[a]) / d2f_est(d[a]);
             tmin = fminf(tmin, tf[a]);
         }
         // a non-finite smallest estimate (a direction component below the
@@ -474,7 +533,7 @@ template <typename R>
 __device__ __forceinline__ void rk4(const Params<R>& p, R kq, const double x[3], const R u[3], R hs, double xo[3],
                                     R uo[3])
 {
-    const R B0 = R(p.B[0]), B1 = R(p.B[1]), B2 = R(p.B[2]);
+    const R B0 = from_d<R>(p.B[0]), B1 = from_d<R>(p.B[1]), B2 = from_d<R>(p.B[2]);
     R a1[3], a2[3], a3[3], a4[3], u2[3], u3[3], u4[3];
     a1[0] = kq * (u[1] * B2 - u[2] * B1);
     a1[1] = kq * (u[2] * B0 - u[0] * B2);
@@ -497,7 +556,7 @@ __device__ __forceinline__ void rk4(const Params<R>& p, R kq, const double x[3],
     R h6 = hs / R(6);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        xo[i] = x[i] + (double)(h6 * (u[i] + R(2) * u2[i] + R(2) * u3[i] + u4[i]));
+        xo[i] = x[i] + to_d(h6 * (u[i] + R(2) * u2[i] + R(2) * u3[i] + u4[i]));
         uo[i] = u[i] + h6 * (a1[i] + R(2) * a2[i] + R(2) * a3[i] + a4[i]);
     }
     R n = msqrt(uo[0] * uo[0] + uo[1] * uo[1] + uo[2] * uo[2]);

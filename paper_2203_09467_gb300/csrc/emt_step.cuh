@@ -185,9 +185,9 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
     R s_max = kInf;
     if (charged && matter) {
         Rng = range_value(p, tab, t.T, lk);
-        R fr_lim = R(p.final_range);
+        R fr_lim = pfinal_range(p);
         R lim = Rng < fr_lim ? Rng : fr_lim;
-        R fr = R(p.step_frac) * Rng;
+        R fr = pstep_frac(p) * Rng;
         s_max = fr > lim ? fr : lim;
     }
     R s_phys = s_max;
@@ -201,26 +201,27 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
     double s;
     bool boundary = false;
     Exit e;
-    double ud[3] = {(double)t.u[0], (double)t.u[1], (double)t.u[2]};
+    const double s_physd = to_d(s_phys);
     if (!(charged && p.has_field)) {
+        const double ud[3] = {to_d(t.u[0]), to_d(t.u[1]), to_d(t.u[2])};
         e = nav_exit(p, t.vol, t.x, ud);
-        if (e.t <= (double)s_phys) {
+        if (e.t <= s_physd) {
             s = e.t;
             boundary = true;
         } else {
-            s = (double)s_phys;
+            s = s_physd;
         }
 #pragma unroll
         for (int a = 0; a < 3; ++a) t.x[a] = t.x[a] + s * ud[a];
         if (boundary && e.axis >= 0) t.x[e.axis] = e.plane;
     } else {
-        double smax = (double)s_phys;
+        double smax = s_physd;
         if (smax > p.max_field_step) {
             smax = p.max_field_step;
             interact = false;
         }
         // at most kMaxSubsteps substeps of h_max per step
-        const double Td = (double)t.T;
+        const double Td = to_d(t.T);
         const double pm = sqrt(Td * (Td + 2.0 * kMe));
         const double hmax = sqrt(8.0 * (pm / (kFieldC * p.bmag)) * p.rk_delta);
         const double cap = kMaxSubsteps * hmax;
@@ -229,7 +230,7 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
             interact = false;
         }
         bool crossed = false;
-        s = propagate_field(p, t.type == 1 ? -1 : 1, (double)t.T, t.vol, t.x, t.u, smax, &e, &crossed);
+        s = propagate_field(p, t.type == 1 ? -1 : 1, Td, t.vol, t.x, t.u, smax, &e, &crossed);
         boundary = crossed;
     }
     if (boundary) interact = false;
@@ -237,13 +238,13 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
     alive = true;
     // 6-7: continuous loss
     if (charged && matter) {
-        R r = Rng - R(s);
+        R r = Rng - from_d<R>(s);
         R Tn = r > R(0) ? inv_range(p, tab, r, lk.n) : R(0);
         R ed = t.T - Tn;
-        fx.dep += (double)ed;
+        fx.dep += to_d(ed);
         t.T = Tn;
-        if (t.T < R(p.cut[t.type])) {
-            fx.dep += (double)t.T + rest_energy(t.type);
+        if (t.T < pcut(p, t.type)) {
+            fx.dep += to_d(t.T) + rest_energy(t.type);
             alive = false;
         }
     }
@@ -251,7 +252,7 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
     if (alive && boundary) {
         t.vol = e.next;
         if (t.vol == kVolOut) {
-            fx.esc = (double)t.T + rest_energy(t.type);
+            fx.esc = to_d(t.T) + rest_energy(t.type);
             alive = false;
         }
         return kNoInteraction;
@@ -271,15 +272,15 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
     }
     const R T = t.T;
     if (t.type == 0) {
-        if (proc == 0) return T > R(p.bk[mi]) ? kPhoto : kNoInteraction;
+        if (proc == 0) return T > from_d<R>(p.bk[mi]) ? kPhoto : kNoInteraction;
         if (proc == 1) return kCompton;
         return T > R(2.0 * kMe) ? kPair : kNoInteraction;
     }
     if (proc == 0) {
-        if (t.type == 1) return T > R(2) * R(p.cut[1]) ? kMoller : kNoInteraction;
-        return T > R(p.cut[1]) ? kBhabha : kNoInteraction;
+        if (t.type == 1) return T > R(2) * pcut(p, 1) ? kMoller : kNoInteraction;
+        return T > pcut(p, 1) ? kBhabha : kNoInteraction;
     }
-    if (proc == 1) return T > R(p.cut[0]) ? kBrems : kNoInteraction;
+    if (proc == 1) return T > pcut(p, 0) ? kBrems : kNoInteraction;
     return kAnnih;
 }
 
@@ -290,7 +291,7 @@ __device__ __forceinline__ void finish_step(const Params<R>& p, TrackReg<R>& t, 
 {
     t.step += 1;
     if (alive && (int)t.step >= p.max_steps) {
-        fx.kill = (double)t.T + rest_energy(t.type);
+        fx.kill = to_d(t.T) + rest_energy(t.type);
         alive = false;
     }
     o.n = 0;
@@ -324,9 +325,9 @@ __device__ __forceinline__ void interaction_part(const Params<R>& p, TrackReg<R>
     pr.local = R(0);
     pr.parent_alive = true;
     const R T = t.T;
-    const R cut_e = R(p.cut[1]), kc = R(p.cut[0]);
+    const R cut_e = pcut(p, 1), kc = pcut(p, 0);
     switch (m) {
-    case kPhoto: sample_photo(T, R(p.bk[p.lmat[t.vol]]), t.u, pr); break;
+    case kPhoto: sample_photo(T, from_d<R>(p.bk[p.lmat[t.vol]]), t.u, pr); break;
     case kCompton: sample_compton(dr, T, t.u, pr, t.T); break;
     case kPair: sample_pair(dr, T, t.u, pr); break;
     case kMoller: sample_moller(dr, T, cut_e, t.u, pr, t.T); break;
@@ -334,7 +335,7 @@ __device__ __forceinline__ void interaction_part(const Params<R>& p, TrackReg<R>
     case kBrems: sample_brems(dr, T, kc, t.u, pr, t.T); break;
     default: sample_annih(dr, T, t.u, pr); break;
     }
-    if (pr.local != R(0)) fx.dep += (double)pr.local;
+    if (pr.local != R(0)) fx.dep += to_d(pr.local);
     int nsec = 0;
     int sec_k[2];
     int sec_type[2];
@@ -343,8 +344,8 @@ __device__ __forceinline__ void interaction_part(const Params<R>& p, TrackReg<R>
     for (int k = 0; k < pr.n; ++k) {
         int st = pr.type[k];
         R sT = pr.T[k];
-        if (sT < R(p.cut[st])) {
-            fx.dep += (double)sT + rest_energy(st);
+        if (sT < pcut(p, st)) {
+            fx.dep += to_d(sT) + rest_energy(st);
             continue;
         }
         sec_type[nsec] = st;
@@ -358,8 +359,8 @@ __device__ __forceinline__ void interaction_part(const Params<R>& p, TrackReg<R>
     bool alive = true;
     if (!pr.parent_alive) {
         alive = false;
-    } else if (t.T < R(p.cut[t.type])) {
-        fx.dep += (double)t.T + rest_energy(t.type);
+    } else if (t.T < pcut(p, t.type)) {
+        fx.dep += to_d(t.T) + rest_energy(t.type);
         alive = false;
     }
     const uint32_t parent_step = t.step;
