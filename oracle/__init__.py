@@ -77,7 +77,9 @@ def lib():
                 "orc_get_table": (i32, [p, i32, i32, i32, p]),
                 "orc_range": (d, [p, i32, i32, d]),
                 "orc_inv_range": (d, [p, i32, i32, d]),
-                "orc_run": (i32, [p, i32, p, p, p, p, p, i32, p, p, p, i32]),
+                "orc_run": (i32, [p, i32, p, p, p, p, p, i32, p, p, p, i32, p, i32]),
+                "orc_nav_exit": (i32, [p, i32, p, p, p]),
+                "orc_locate": (i32, [p, p]),
                 "orc_step_one": (i32, [p, p, u64, u64, p, p, p]),
             }
             for name, (res, args) in sig.items():
@@ -135,15 +137,20 @@ class Oracle:
     physics   : (9,)    cut_g, cut_em, cut_ep, e_lo, e_hi, bins_per_decade,
                         step_frac, final_range, process_mask
     layers    : (L, 3)  material, thickness_cm, score_bin
-    world     : (16,)   z0, half_x, half_y, wlo[3], whi[3], B[3],
-                        rk_delta_cm, max_steps, n_bins, max_field_step_cm
+    world     : (21,)   z0, half_x, half_y, wlo[3], whi[3], B[3],
+                        rk_delta_cm, max_steps, n_bins, max_field_step_cm,
+                        geometry (0 layers, 1 cylinders), half_z_cm,
+                        score_z, score_z_lo_cm, score_z_hi_cm
+                        (a 16-entry world is layers scored per volume)
     """
 
     def __init__(self, materials, physics, layers, world, seed: int):
         self.materials = np.ascontiguousarray(materials, np.float64).reshape(-1, 5)
         self.physics = np.ascontiguousarray(physics, np.float64)
         self.layers = np.ascontiguousarray(layers, np.float64).reshape(-1, 3)
-        self.world = np.ascontiguousarray(world, np.float64)
+        w = np.zeros(21)
+        w[: len(world)] = np.asarray(world, np.float64)
+        self.world = w
         self.seed = int(seed)
         self.n_bins = int(self.world[14])
         h = lib().orc_create(_ptr(self.materials), len(self.materials), _ptr(self.physics),
@@ -182,8 +189,21 @@ class Oracle:
     def inv_range(self, m, ci, r) -> float:
         return lib().orc_inv_range(self._h, m, ci, r)
 
-    def run(self, prim: dict, n_events: int, event_ids, n_threads: int = 0):
-        """Transport all events; returns (hist[n_events, n_bins], summary[n_events, 6])."""
+    def nav_exit(self, vol: int, p, d):
+        """(t, next volume) of the exit from volume vol along d from p."""
+        pp = np.ascontiguousarray(p, np.float64)
+        dd = np.ascontiguousarray(d, np.float64)
+        t = np.zeros(1)
+        nxt = lib().orc_nav_exit(self._h, vol, _ptr(pp), _ptr(dd), _ptr(t))
+        return float(t[0]), int(nxt)
+
+    def locate(self, p) -> int:
+        pp = np.ascontiguousarray(p, np.float64)
+        return int(lib().orc_locate(self._h, _ptr(pp)))
+
+    def run(self, prim: dict, n_events: int, event_ids, n_threads: int = 0, step_bins: int = 0):
+        """Transport all events; returns (hist[n_events, n_bins], summary[n_events, 6]),
+        plus the steps-per-track histogram [3, step_bins] when step_bins > 0."""
         ev = np.ascontiguousarray(prim["event"], np.int32)
         ty = np.ascontiguousarray(prim["type"], np.int32)
         T = np.ascontiguousarray(prim["T"], np.float64)
@@ -192,10 +212,14 @@ class Oracle:
         ids = np.ascontiguousarray(event_ids, np.uint64)
         hist = np.zeros((n_events, self.n_bins))
         summ = np.zeros((n_events, 6))
+        sh = np.zeros((3, max(step_bins, 1)), np.uint64)
         rc = lib().orc_run(self._h, len(ev), _ptr(ev), _ptr(ty), _ptr(T), _ptr(pos), _ptr(d),
-                           n_events, _ptr(ids), _ptr(hist), _ptr(summ), n_threads)
+                           n_events, _ptr(ids), _ptr(hist), _ptr(summ), n_threads,
+                           _ptr(sh) if step_bins > 0 else None, step_bins)
         if rc != 0:
             raise ValueError("orc_run failed")
+        if step_bins > 0:
+            return hist, summ, sh
         return hist, summ
 
     def step_one(self, track, uid: int, event_id: int, with_uids: bool = False):

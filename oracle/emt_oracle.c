@@ -440,6 +440,10 @@ struct orc_handle {
     int n_bins;
     double max_field_step;
     int has_field;
+    int geom;      /* GEOM_LAYERS or GEOM_CYLINDERS */
+    double half_z; /* cylinders: the stack spans |z| <= half_z */
+    int score_z;   /* 1: histogram bins along z; 0: bins per volume */
+    double zs_lo, zs_w;
     uint32_t seed;
 };
 
@@ -636,6 +640,16 @@ orc_handle* orc_create(const double* materials, int n_mat, const double* physics
     h->n_bins = (int)world[14];
     h->max_field_step = world[15];
     h->has_field = (h->B[0] != 0.0 || h->B[1] != 0.0 || h->B[2] != 0.0);
+    h->geom = (int)world[16];
+    h->half_z = world[17];
+    h->score_z = (int)world[18];
+    h->zs_lo = world[19];
+    h->zs_w = (world[20] - world[19]) / (double)h->n_bins;
+    if ((h->geom != 0 && h->geom != 1) || (h->geom == 1 && (h->zb[0] != 0.0 || !(h->half_z > 0.0))) ||
+        (h->score_z && !(world[20] > world[19]))) {
+        orc_destroy(h);
+        return NULL;
+    }
     h->seed = seed;
     build_tables(h);
     return h;
@@ -660,13 +674,20 @@ int orc_get_table(const orc_handle* h, int m, int p, int q, double* out)
 }
 
 /* ------------------------------------------------------------------ */
-/* Geometry: layers stacked along +z from z0 inside |x|<=hx, |y|<=hy;  */
+/* Geometry (a reading of Sec. 3.3: the paper navigates CMS with       */
+/* VecGeom or ORANGE, a CSG of quadric surfaces; this build has two    */
+/* kinds of volumes with exact logical volume indices).                */
+/* Layers: slabs stacked along +z from z0 inside |x|<=hx, |y|<=hy;     */
 /* volume -1 is the vacuum of the world box; -2 is outside the world.  */
-/* A reading of Sec. 3.3 (the paper uses VecGeom/ORANGE on CMS; this   */
-/* build uses layered boxes with exact logical volume indices).        */
+/* Cylinders: concentric shells about the z axis (Sec. 4's test        */
+/* problem), shell i spanning zb[i] <= rho < zb[i+1] and |z| <= half_z,*/
+/* zb[0] = 0; leaving the outermost shell or the end planes leaves the */
+/* world (-2).                                                         */
 /* ------------------------------------------------------------------ */
 #define VOL_WORLD (-1)
 #define VOL_OUT (-2)
+#define GEOM_LAYERS 0
+#define GEOM_CYLINDERS 1
 
 typedef struct {
     double t;
@@ -684,9 +705,65 @@ static int layer_at(const orc_handle* h, double z)
     return j;
 }
 
+/* Cylinders: exit parameter along d (any length) from p in shell vol.
+ * Candidates in the order end plane, outer surface, inner surface; the
+ * smallest wins, ties to the earlier.  A surface rho = r meets the line
+ * p + t d where a t^2 + 2 b t + c = 0, with a = dx^2 + dy^2,
+ * b = px dx + py dy, c = px^2 + py^2 - r^2.  Outer surface (c <= 0): the
+ * larger root, (sqrt(b^2 - a c) - b)/a, written -c/(b + sqrt(b^2 - a c))
+ * when b > 0 to avoid cancellation.  Inner surface: only when moving
+ * inward (b < 0) and the discriminant is non-negative, the smaller root
+ * c/(sqrt(b^2 - a c) - b).  Crossing a radial surface moves the track to
+ * the neighbouring shell; the end planes and the outermost surface lead
+ * out of the world. */
+static exit_t nav_exit_cyl(const orc_handle* h, int vol, const double p[3], const double d[3])
+{
+    exit_t e = {INF_D, VOL_OUT, -1, 0.0};
+    if (d[2] != 0.0) {
+        double pl = d[2] > 0.0 ? h->half_z : -h->half_z;
+        e.t = (pl - p[2]) / d[2];
+        e.axis = 2;
+        e.plane = pl;
+    }
+    double a = d[0] * d[0] + d[1] * d[1];
+    if (a > 0.0) {
+        double b = p[0] * d[0] + p[1] * d[1];
+        double q = p[0] * p[0] + p[1] * p[1];
+        double ro = h->zb[vol + 1];
+        double c = q - ro * ro;
+        double disc = b * b - a * c;
+        if (disc < 0.0) disc = 0.0;
+        double sq = sqrt(disc);
+        double t = b > 0.0 ? -c / (b + sq) : (sq - b) / a;
+        if (t < e.t) {
+            e.t = t;
+            e.axis = -1;
+            e.plane = 0.0;
+            e.next = vol + 1 < h->n_layers ? vol + 1 : VOL_OUT;
+        }
+        if (vol > 0 && b < 0.0) {
+            double ri = h->zb[vol];
+            double ci = q - ri * ri;
+            double di = b * b - a * ci;
+            if (di >= 0.0) {
+                double ti = ci / (sqrt(di) - b);
+                if (ti < e.t) {
+                    e.t = ti;
+                    e.axis = -1;
+                    e.plane = 0.0;
+                    e.next = vol - 1;
+                }
+            }
+        }
+    }
+    if (e.t < 0.0) e.t = 0.0;
+    return e;
+}
+
 /* exit parameter t >= 0 along d (any length) from point p in volume vol */
 static exit_t nav_exit(const orc_handle* h, int vol, const double p[3], const double d[3])
 {
+    if (h->geom == GEOM_CYLINDERS) return nav_exit_cyl(h, vol, p, d);
     exit_t e = {INF_D, VOL_OUT, -1, 0.0};
     if (vol >= 0) {
         int L = h->n_layers;
@@ -765,6 +842,14 @@ static exit_t nav_exit(const orc_handle* h, int vol, const double p[3], const do
 /* logical volume of a starting point (primaries) */
 static int locate(const orc_handle* h, const double p[3])
 {
+    if (h->geom == GEOM_CYLINDERS) {
+        double q = p[0] * p[0] + p[1] * p[1];
+        double rmax = h->zb[h->n_layers];
+        if (!(p[2] >= -h->half_z && p[2] <= h->half_z) || !(q < rmax * rmax)) return VOL_OUT;
+        int j = 0;
+        while (j + 1 < h->n_layers && h->zb[j + 1] * h->zb[j + 1] <= q) ++j;
+        return j;
+    }
     if (p[0] >= -h->hx && p[0] <= h->hx && p[1] >= -h->hy && p[1] <= h->hy && p[2] >= h->zb[0] &&
         p[2] <= h->zb[h->n_layers])
         return layer_at(h, p[2]);
@@ -1153,7 +1238,7 @@ static double propagate_field(const orc_handle* h, int charge, double T, int vol
         if (e.t <= 1.0) {
             double h2 = hs * e.t;
             rk4(h, kq, x, u, h2, x1, u1);
-            x1[e.axis] = e.plane;
+            if (e.axis >= 0) x1[e.axis] = e.plane;
             memcpy(x, x1, sizeof x1);
             memcpy(u, u1, sizeof u1);
             s += h2;
@@ -1186,13 +1271,28 @@ typedef struct {
     double n_steps, n_tracks;
 } tally_t;
 
-static void deposit(const orc_handle* h, tally_t* t, int vol, double e)
+/* histogram bin of a deposit made in volume vol at height z: the
+ * volume's score bin, or with scoring along z the bin of z among n_bins
+ * equal bins of [zs_lo, zs_hi); -1 = no bin (the deposit still counts in
+ * edep) */
+static int score_bin(const orc_handle* h, int vol, double z)
+{
+    if (h->score_z) {
+        double f = floor((z - h->zs_lo) / h->zs_w);
+        return (f >= 0.0 && f < (double)h->n_bins) ? (int)f : -1;
+    }
+    if (vol < 0) return -1;
+    int b = h->layer_bin[vol];
+    return (b >= 0 && b < h->n_bins) ? b : -1;
+}
+
+/* every deposit of a step is made at the post-step point, in the volume
+ * the step started in */
+static void deposit(const orc_handle* h, tally_t* t, int vol, double z, double e)
 {
     t->edep += e;
-    if (vol >= 0) {
-        int b = h->layer_bin[vol];
-        if (b >= 0 && b < h->n_bins) t->hist[b] += e;
-    }
+    int b = score_bin(h, vol, z);
+    if (b >= 0) t->hist[b] += e;
 }
 
 static double rest_energy(int type) { return type == 2 ? 2.0 * ME : 0.0; }
@@ -1296,12 +1396,12 @@ static void step_track(const orc_handle* h, uint64_t event_id, track_t* tr, tall
         double r = R - s;
         double Tn = r > 0.0 ? inv_range_of(h, tab(h, mi, tr->type, 3), r) : 0.0;
         double ed = tr->T - Tn;
-        deposit(h, ta, tr->vol, ed);
+        deposit(h, ta, tr->vol, tr->x[2], ed);
         res->edep += ed;
         tr->T = Tn;
         if (tr->T < h->cut[tr->type]) {
             double e2 = tr->T + rest_energy(tr->type);
-            deposit(h, ta, tr->vol, e2);
+            deposit(h, ta, tr->vol, tr->x[2], e2);
             res->edep += e2;
             alive = 0;
         }
@@ -1375,7 +1475,7 @@ static void step_track(const orc_handle* h, uint64_t event_id, track_t* tr, tall
         case P_ANNIH: sample_annih(&dr, T, tr->u, &pr); break;
         }
         if (pr.local != 0.0) {
-            deposit(h, ta, tr->vol, pr.local);
+            deposit(h, ta, tr->vol, tr->x[2], pr.local);
             res->edep += pr.local;
         }
         for (int k = 0; k < pr.n; ++k) {
@@ -1383,7 +1483,7 @@ static void step_track(const orc_handle* h, uint64_t event_id, track_t* tr, tall
             double sT = pr.T[k];
             if (sT < h->cut[st]) {
                 double e2 = sT + rest_energy(st);
-                deposit(h, ta, tr->vol, e2);
+                deposit(h, ta, tr->vol, tr->x[2], e2);
                 res->edep += e2;
                 continue;
             }
@@ -1401,7 +1501,7 @@ static void step_track(const orc_handle* h, uint64_t event_id, track_t* tr, tall
                 alive = 0;
             } else if (tr->T < h->cut[tr->type]) {
                 double e2 = tr->T + rest_energy(tr->type);
-                deposit(h, ta, tr->vol, e2);
+                deposit(h, ta, tr->vol, tr->x[2], e2);
                 res->edep += e2;
                 alive = 0;
             }
@@ -1433,7 +1533,8 @@ static void push(stack_t_* s, const track_t* t)
 /* transport one event depth-first from a stack (order does not change
  * any result: every track draws from its own counter-based stream) */
 static void run_event(const orc_handle* h, uint64_t event_id, int n, const int* idx, const int32_t* type,
-                      const double* T, const double* pos, const double* dir, tally_t* ta)
+                      const double* T, const double* pos, const double* dir, tally_t* ta, uint64_t* step_hist,
+                      int step_bins)
 {
     stack_t_ st = {NULL, 0, 0};
     for (int i = n - 1; i >= 0; --i) {
@@ -1454,7 +1555,7 @@ static void run_event(const orc_handle* h, uint64_t event_id, int n, const int* 
             continue;
         }
         if (t.T < h->cut[t.type]) {
-            deposit(h, ta, t.vol, t.T + rest_energy(t.type));
+            deposit(h, ta, t.vol, t.x[2], t.T + rest_energy(t.type));
             continue;
         }
         push(&st, &t);
@@ -1469,9 +1570,23 @@ static void run_event(const orc_handle* h, uint64_t event_id, int n, const int* 
             for (int k = r.n_sec - 1; k >= 0; --k) push(&st, &r.sec[k]);
             if (!r.alive) break;
         }
+        /* steps per track by particle type (Sec. 4 diagnostics) */
+        if (step_hist) {
+            uint32_t b = t.step < (uint32_t)(step_bins - 1) ? t.step : (uint32_t)(step_bins - 1);
+            step_hist[(size_t)t.type * step_bins + b] += 1;
+        }
     }
     free(st.v);
 }
+
+int orc_nav_exit(const orc_handle* h, int vol, const double* p, const double* d, double* t)
+{
+    exit_t e = nav_exit(h, vol, p, d);
+    *t = e.t;
+    return e.next;
+}
+
+int orc_locate(const orc_handle* h, const double* p) { return locate(h, p); }
 
 int orc_step_one(orc_handle* h, double* trk, uint64_t uid, uint64_t event_id, double* sec, uint64_t* sec_uid,
                  double* info)
@@ -1533,6 +1648,8 @@ typedef struct {
     const double *T, *pos, *dir;
     double* hist;
     double* summary;
+    uint64_t* step_hist; /* [3][step_bins] or NULL */
+    int step_bins;
     volatile int next;
     pthread_mutex_t mu;
 } job_t;
@@ -1540,6 +1657,7 @@ typedef struct {
 static void* worker(void* arg)
 {
     job_t* j = (job_t*)arg;
+    uint64_t* sh = j->step_hist ? (uint64_t*)calloc((size_t)3 * j->step_bins, sizeof(uint64_t)) : NULL;
     for (;;) {
         pthread_mutex_lock(&j->mu);
         int e = j->next++;
@@ -1550,7 +1668,7 @@ static void* worker(void* arg)
         ta.hist = j->hist + (size_t)e * j->h->n_bins;
         memset(ta.hist, 0, sizeof(double) * j->h->n_bins);
         int b = j->start[e], n = j->start[e + 1] - b;
-        run_event(j->h, j->event_ids[e], n, j->order + b, j->type, j->T, j->pos, j->dir, &ta);
+        run_event(j->h, j->event_ids[e], n, j->order + b, j->type, j->T, j->pos, j->dir, &ta, sh, j->step_bins);
         double* s = j->summary + 6 * (size_t)e;
         s[0] = ta.edep;
         s[1] = ta.escaped;
@@ -1559,13 +1677,20 @@ static void* worker(void* arg)
         s[4] = ta.n_steps;
         s[5] = ta.n_tracks;
     }
+    if (sh) {
+        pthread_mutex_lock(&j->mu);
+        for (int k = 0; k < 3 * j->step_bins; ++k) j->step_hist[k] += sh[k];
+        pthread_mutex_unlock(&j->mu);
+        free(sh);
+    }
     return NULL;
 }
 
 int orc_run(orc_handle* h, int n_prim, const int32_t* ev, const int32_t* type, const double* T,
             const double* pos, const double* dir, int n_events, const uint64_t* event_ids, double* hist,
-            double* summary, int n_threads)
+            double* summary, int n_threads, uint64_t* step_hist, int step_bins)
 {
+    if (step_hist && step_bins < 1) return -1;
     if (n_events <= 0) return 0;
     int* start = (int*)calloc((size_t)n_events + 1, sizeof(int));
     int* order = (int*)malloc(sizeof(int) * (size_t)(n_prim > 0 ? n_prim : 1));
@@ -1593,6 +1718,8 @@ int orc_run(orc_handle* h, int n_prim, const int32_t* ev, const int32_t* type, c
     j.dir = dir;
     j.hist = hist;
     j.summary = summary;
+    j.step_hist = step_hist;
+    j.step_bins = step_bins;
     j.next = 0;
     pthread_mutex_init(&j.mu, NULL);
     if (n_threads <= 0) n_threads = (int)sysconf(_SC_NPROCESSORS_ONLN);

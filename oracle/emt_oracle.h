@@ -73,7 +73,16 @@ int orc_sample(int process, double E, double cut_e, double cut_g, uint32_t seed,
  *             final_range, process_mask}
  * layers   : n_layers x {material, thickness_cm, score_bin}
  * world    : {z0, half_x, half_y, wlo[3], whi[3], B[3], rk_delta_cm,
- *             max_steps, n_bins, max_field_step_cm}                         */
+ *             max_steps, n_bins, max_field_step_cm, geometry, half_z_cm,
+ *             score_z, score_z_lo_cm, score_z_hi_cm}
+ *   geometry 0: layers are slabs stacked along +z from z0 inside
+ *               |x| <= half_x, |y| <= half_y, in the world box wlo..whi;
+ *   geometry 1: layers are concentric cylindrical shells about the z axis,
+ *               radii accumulated from z0 (must be 0), |z| <= half_z; the
+ *               outermost shell and the end planes bound the world.
+ *   score_z 0 : histogram bin = the score bin of the deposit's volume;
+ *   score_z 1 : n_bins equal bins of z over [score_z_lo, score_z_hi).
+ * Returns NULL for an invalid configuration.                                */
 orc_handle* orc_create(const double* materials, int n_mat, const double* physics,
                        const double* layers, int n_layers, const double* world,
                        uint32_t seed);
@@ -93,11 +102,19 @@ double orc_inv_range(const orc_handle*, int m, int charge_index, double r);
  * T[n], pos[3n], dir[3n]; event_ids[n_events].
  * outputs: hist[n_events*n_bins]; summary[n_events*6] =
  *   {edep, escaped, killed, e_in, n_steps, n_tracks}
- * n_threads <= 0 : all available cores.                                     */
+ * n_threads <= 0 : all available cores.
+ * step_hist (optional, NULL = off): adds the number of steps of every
+ * transported track, by particle type, into step_hist[3][step_bins]
+ * (counts of step_bins - 1 or more steps in the last bin).                  */
 int orc_run(orc_handle*, int n_prim, const int32_t* ev, const int32_t* type,
             const double* T, const double* pos, const double* dir,
             int n_events, const uint64_t* event_ids, double* hist,
-            double* summary, int n_threads);
+            double* summary, int n_threads, uint64_t* step_hist, int step_bins);
+
+/* geometry pins: exit parameter along d from p in volume vol (returns the
+ * next volume, writes t), and the volume of a starting point */
+int orc_nav_exit(const orc_handle*, int vol, const double* p, const double* d, double* t);
+int orc_locate(const orc_handle*, const double* p);
 
 /* one step of one track (diagnostics and single-step pins).
  * track in/out: {type, T, x, y, z, ux, uy, uz, vol, step}, uid, event_id.

@@ -4,8 +4,8 @@ This module holds input data only (material constants, layer stacks and the
 random primaries of each workload); it contains none of the transport
 arithmetic, and both the GPU library and the CPU oracle are fed from it.
 
-Workloads (the paper's own CMS-like test problem, Sec. 4, is not used; these
-are synthetic calorimeter workloads of the same kind):
+Workloads (synthetic calorimeter workloads, plus the paper's own test
+problem of Sec. 4 with its unstated dimensions read as below):
 
   slab      1,000 events x one 100 MeV e- along +z into a 5 cm Pb slab,
             20x20 cm, no field, one score bin.
@@ -17,6 +17,14 @@ are synthetic calorimeter workloads of the same kind):
   batched   256 events of 1-64 primaries, e-/e+/gamma, 0.1-100 GeV
             log-uniform, on the calo_field geometry.
   served    Poisson arrivals; 1-100 primaries per event, 1-50 GeV.
+  cms       the paper's verification problem (Sec. 4): six concentric
+            cylindrical shells about the z axis out to 375 cm, each one
+            element (vacuum, Si, Pb, C, Ti, Fe), no field; 100 events x 1000
+            photons of 1 GeV from an isotropic point source at the origin;
+            energy deposition tallied along z.  The paper gives only the
+            outer radius: the shell radii (30, 125, 175, 275, 325, 375 cm)
+            and the half-length (700 cm) are readings of a CMS-like layout.
+  cms_field the cms geometry in a uniform 3.8 T field along z.
 """
 from __future__ import annotations
 
@@ -30,6 +38,10 @@ import numpy as np
 VACUUM = (0.0, 1.0, 0.0, 1.0, 0.0)
 LEAD = (82.0, 207.2, 11.35, 823.0, 0.0880)
 LIQUID_ARGON = (18.0, 39.948, 1.396, 188.0, 0.0032)
+SILICON = (14.0, 28.0855, 2.329, 173.0, 0.001839)
+CARBON = (6.0, 12.0107, 2.21, 78.0, 0.000284)     # graphite
+TITANIUM = (22.0, 47.867, 4.54, 233.0, 0.004966)
+IRON = (26.0, 55.845, 7.874, 286.0, 0.007112)
 
 GAMMA, ELECTRON, POSITRON = 0, 1, 2
 
@@ -41,7 +53,8 @@ class Setup:
     materials: np.ndarray      # (n, 5)
     physics: np.ndarray        # (9,)  cut_g, cut_em, cut_ep, e_lo, e_hi, bpd, step_frac, final_range, mask
     layers: np.ndarray         # (L, 3) material, thickness_cm, score_bin
-    world: np.ndarray          # (16,) z0, half_x, half_y, wlo[3], whi[3], B[3], rk_delta, max_steps, n_bins, max_field_step
+    world: np.ndarray          # (21,) z0, half_x, half_y, wlo[3], whi[3], B[3], rk_delta, max_steps, n_bins,
+    #                            max_field_step, geometry, half_z, score_z, score_z_lo, score_z_hi
     seed: int
 
     @property
@@ -53,10 +66,15 @@ def physics(cut=1.0, mask=63, e_lo=1e-3, e_hi=1e5, bpd=8, step_frac=0.2, final_r
     return np.array([cut, cut, cut, e_lo, e_hi, bpd, step_frac, final_range, mask], np.float64)
 
 
+GEOM_LAYERS, GEOM_CYLINDERS = 0, 1
+
+
 def world(z0, half_x, half_y, wlo, whi, B=(0.0, 0.0, 0.0), rk_delta=1e-5, max_steps=100000,
-          n_bins=100, max_field_step=10.0):
-    return np.array([z0, half_x, half_y, *wlo, *whi, *B, rk_delta, max_steps, n_bins, max_field_step],
-                    np.float64)
+          n_bins=100, max_field_step=10.0, geometry=GEOM_LAYERS, half_z=0.0, score_z=None):
+    """score_z: None scores per volume; (lo, hi) scores n_bins equal bins of z."""
+    zs = (0, 0.0, 0.0) if score_z is None else (1, float(score_z[0]), float(score_z[1]))
+    return np.array([z0, half_x, half_y, *wlo, *whi, *B, rk_delta, max_steps, n_bins, max_field_step,
+                     geometry, half_z, *zs], np.float64)
 
 
 def slab_setup(seed=1, mask=63, cut=1.0, thickness=5.0) -> Setup:
@@ -89,6 +107,27 @@ def calo_field_setup(seed=3, mask=63, n_pairs=50, B=2.0) -> Setup:
     w = world(0.0, 20.0, 20.0, (-25.0, -25.0, -5.0), (25.0, 25.0, depth + 5.0), B=(B, 0.0, 0.0),
               n_bins=100, max_field_step=10.0)
     return Setup("calo_field", mats, physics(mask=mask), layers, w, seed)
+
+
+CMS_RADII = (30.0, 125.0, 175.0, 275.0, 325.0, 375.0)
+CMS_HALF_Z = 700.0
+
+
+def cms_setup(seed=6, mask=63, B=0.0, n_bins=140) -> Setup:
+    """Six single-element shells (vacuum, Si, Pb, C, Ti, Fe); layers are
+    radial shells (thickness = radial extent), scored along z over the
+    full length in n_bins bins."""
+    mats = np.array([VACUUM, SILICON, LEAD, CARBON, TITANIUM, IRON], np.float64)
+    r = (0.0,) + CMS_RADII
+    layers = np.array([[i, r[i + 1] - r[i], i] for i in range(6)], np.float64)
+    w = world(0.0, 0.0, 0.0, (0.0, 0.0, 0.0), (0.0, 0.0, 0.0), B=(0.0, 0.0, B), n_bins=n_bins,
+              max_field_step=10.0, geometry=GEOM_CYLINDERS, half_z=CMS_HALF_Z,
+              score_z=(-CMS_HALF_Z, CMS_HALF_Z))
+    return Setup("cms" if B == 0.0 else "cms_field", mats, physics(mask=mask), layers, w, seed)
+
+
+def cms_field_setup(seed=7, mask=63, B=3.8) -> Setup:
+    return cms_setup(seed=seed, mask=mask, B=B)
 
 
 # ---------------------------------------------------------------- primaries
@@ -139,6 +178,24 @@ def calo_field_primaries(n_events=10000, seed=3, e_min=1000.0, e_ratio=100.0):
     pos = np.concatenate([xy, np.full((n, 1), -1.0)], axis=1)
     return _finish({"event": np.arange(n), "type": types, "T": T, "pos": pos,
                     "dir": _cone_dirs(rng, n, 10.0)})
+
+
+def isotropic_dirs(rng, n):
+    """Directions uniform on the unit sphere."""
+    cost = 2.0 * rng.random(n) - 1.0
+    phi = 2.0 * np.pi * rng.random(n)
+    sint = np.sqrt(np.maximum(0.0, 1.0 - cost * cost))
+    return np.stack([sint * np.cos(phi), sint * np.sin(phi), cost], axis=1)
+
+
+def cms_primaries(n_events=100, per_event=1000, energy=1000.0, seed=6, particle=GAMMA):
+    """Isotropic point source at the origin: per_event photons of `energy`
+    per event."""
+    rng = np.random.default_rng(seed)
+    n = n_events * per_event
+    return _finish({
+        "event": np.repeat(np.arange(n_events), per_event), "type": np.full(n, particle),
+        "T": np.full(n, energy), "pos": np.zeros((n, 3)), "dir": isotropic_dirs(rng, n)})
 
 
 def multi_primaries(n_events, n_min, n_max, e_min, e_ratio, seed, max_deg=10.0):
