@@ -72,6 +72,11 @@ def workload(name, n_events, rank):
         s.seed = 5
         prim = W.served_primaries(n_events, seed=5 + 7919 * rank)
         desc = f"calorimeter in 2 T field, {n_events} requests of 1-100 primaries, 1-50 GeV"
+    elif name in ("cms", "cms_field"):
+        s = W.cms_setup() if name == "cms" else W.cms_field_setup()
+        prim = W.cms_primaries(n_events, 1000, seed=s.seed + 7919 * rank)
+        desc = (f"CMS-like 6 cylindrical shells to 375 cm (vacuum, Si, Pb, C, Ti, Fe)"
+                f"{', 3.8 T along z' if name == 'cms_field' else ''}, {n_events} events x 1000 isotropic 1 GeV photons")
     else:
         raise SystemExit(f"unknown workload {name}")
     ids = (np.arange(n_events, dtype=np.uint64) + np.uint64(rank * n_events))
@@ -422,12 +427,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="emt", choices=["emt", "reference"])
-    ap.add_argument("--workload", default="calo", choices=["calo", "slab", "calo_field", "batched", "served"])
+    ap.add_argument("--workload", default="calo",
+                    choices=["calo", "slab", "calo_field", "batched", "served", "cms", "cms_field"])
     ap.add_argument("--rates", default="10,100,1000", help="served: request rates (Hz)")
     ap.add_argument("--duration", type=float, default=60.0, help="served: seconds of requests per rate")
     ap.add_argument("--serve-slots", type=int, default=1 << 22, help="served: track-slot pool")
     ap.add_argument("--serve-events", type=int, default=4096, help="served: event slots")
-    ap.add_argument("--events", type=int, default=10000)
+    ap.add_argument("--events", type=int, default=None, help="default 10,000 (100 for cms, cms_field)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--loop", default="auto", choices=["auto", "plain", "graph"],
                     help="auto: autotune block size and loop driver on the workload first")
@@ -445,6 +451,8 @@ def main():
     ap.add_argument("--traffic-per-launch", type=float, default=None,
                     help="DRAM bytes per step-kernel launch from an ncu capture of this kernel")
     args = ap.parse_args()
+    if args.events is None:
+        args.events = 100 if args.workload in ("cms", "cms_field") else 10000
     if args.impl == "reference":
         reference_arm(args)
     elif args.workload == "served":

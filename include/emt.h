@@ -9,7 +9,8 @@
  * cutoffs (Sec. 3.2 list of capabilities), the six electromagnetic models
  * of Table 1 (Klein-Nishina, Bethe-Heitler, photoelectric, bremsstrahlung,
  * Moller-Bhabha, two-photon annihilation), straight-line and uniform-field
- * propagation through layered-box geometry (Sec. 3.3), secondary
+ * propagation through layered-box or concentric-cylinder geometry (Sec. 3.3;
+ * the cylinders are Sec. 4's CMS-like test problem), secondary
  * allocation with a capacity-bounded device stack (Sec. 3.1, "function-like
  * stack allocator ... atomic addition", with out-of-memory handled without
  * breaking reproducibility), and scoring in device kernels instead of host
@@ -96,7 +97,24 @@ typedef struct emt_options {
     void* cuda_stream;     /* cudaStream_t to use, or NULL for a context-owned stream */
     void* device_pool;     /* caller-owned device memory, or NULL: see emt_pool_bytes */
     size_t pool_bytes;
+    int32_t step_hist_bins; /* > 0: keep the steps-per-track histogram (Sec. 4 diagnostics),
+                               emt_read_step_hist; 0: off (no cost) */
+    int32_t select_policy;  /* EMT_SELECT_*: which tracks step when more than max_active are in flight */
+    int64_t max_active;     /* > 0: at most this many tracks step per iteration, the others are
+                               held unchanged (split schedule only); 0: every track steps */
 } emt_options;
+
+/* Track selection (Sec. 4: "preferentially selecting lower-energy particles
+ * for tracking ... could reduce the total capacity requirement").  Held
+ * tracks keep their step counter, so they draw the same random numbers
+ * when they step later: results do not depend on the policy or the budget
+ * (up to the summation order of deposits).
+ * ORDER: the first max_active tracks of the input (photons, then charged).
+ * LOW_ENERGY: the max_active tracks of lowest kinetic energy, by quarter-
+ *   octave energy classes counted as each step writes its outputs (ties in
+ *   the last class admitted are broken arbitrarily). */
+#define EMT_SELECT_ORDER 0
+#define EMT_SELECT_LOW_ENERGY 1
 
 /* Fill `opt` with defaults (device 0, FP64, 2^22 slots, 10,000 events,
  * 128 bins, plain loop, seed 1). */
@@ -147,6 +165,21 @@ typedef struct emt_layer {
     double thickness_cm;
 } emt_layer;
 
+/* Geometry kinds (Sec. 3.3; the paper's navigators are VecGeom and ORANGE,
+ * a CSG of quadric surfaces, which this library replaces by two volume
+ * kinds with exact logical volume indices):
+ * LAYERS: layer i is the slab zb[i] <= z < zb[i+1] (zb[0] = z0, zb[i+1] =
+ *   zb[i] + thickness) within |x| <= half_x, |y| <= half_y, inside the world
+ *   box lo..hi of vacuum; leaving the box leaves the world.
+ * CYLINDERS: layer i is the shell zb[i] <= rho < zb[i+1] about the z axis
+ *   (radii accumulated from z0, which must be 0; the first layer is a solid
+ *   cylinder) for |z| <= half_z; leaving the outermost shell or the end
+ *   planes leaves the world (the envelope is the world).  half_x, half_y,
+ *   lo and hi are ignored.  This is the geometry of Sec. 4's test problem
+ *   (six single-element shells out to 375 cm). */
+#define EMT_GEOM_LAYERS 0
+#define EMT_GEOM_CYLINDERS 1
+
 typedef struct emt_world {
     double z0_cm, half_x_cm, half_y_cm;
     double lo_cm[3], hi_cm[3];
@@ -155,9 +188,16 @@ typedef struct emt_world {
     double max_field_step_cm; /* longest path of one step in a field */
     int32_t max_steps;        /* per-track step limit; then the track is killed */
     int32_t n_bins;           /* histogram width (<= options.max_bins) */
+    int32_t geometry;         /* EMT_GEOM_* */
+    int32_t score_z;          /* 0: bin = the layer's score_bin; 1: n_bins equal bins of z
+                                 over [score_z_lo, score_z_hi) (Sec. 4 tallies the
+                                 deposition along z) */
+    double half_z_cm;         /* CYLINDERS: half-length */
+    double score_z_lo_cm, score_z_hi_cm;
 } emt_world;
 
-/* host: layers[n], world.  n in [1, 4096]. */
+/* host: layers[n], world.  n in [1, 4096].  Every deposit of a step is
+ * made at the step's end point, in the volume the step started in. */
 emt_status emt_load_geometry(emt_ctx* ctx, const emt_layer* layers, int32_t n, const emt_world* world);
 
 /* Primaries of a batch of events, structure of arrays, n entries:
@@ -190,11 +230,41 @@ typedef struct emt_run_stats {
     double kernel_ms;     /* device time of the step-kernel launches (CUDA events
                              around each launch, or each graph launch) */
     int32_t kernel_launches;
+    int64_t held;         /* track copies held back by the track selection */
 } emt_run_stats;
 
 /* Step every track in flight until none is left or max_iterations
  * (<= 0: no limit) iterations have run.  stats may be NULL. */
 emt_status emt_run(emt_ctx* ctx, int32_t max_iterations, emt_run_stats* stats);
+
+/* Per-step diagnostics (Sec. 4, tracks in flight and time per step): as
+ * emt_run with the plain driver, recording for each iteration the photons
+ * and charged tracks in flight at its start, the tracks queued for an
+ * interaction (split schedule; -1 under the fused one), the track-steps
+ * deferred for lack of output capacity, the tracks held back by the track
+ * selection (emt_options.max_active), and the device time of the step's
+ * launches.  host rec[cap]; *n_rec = records written (iterations beyond
+ * cap are run but not recorded). */
+typedef struct emt_step_record {
+    int64_t photons;
+    int64_t charged;
+    int64_t interacting;
+    int64_t deferred;
+    int64_t held;  /* held back by the track selection */
+    double ms;
+} emt_step_record;
+
+emt_status emt_run_traced(emt_ctx* ctx, int32_t max_iterations, emt_run_stats* stats, emt_step_record* rec,
+                          int32_t cap, int32_t* n_rec);
+
+/* Steps-per-track histogram (Sec. 4: steps per track by particle type),
+ * kept when emt_options.step_hist_bins > 0: host out[3][step_hist_bins],
+ * counts of finished tracks by type (0 gamma, 1 e-, 2 e+) and number of
+ * steps, tracks of step_hist_bins - 1 or more steps in the last bin,
+ * accumulated over every run since the context was created or the last
+ * reset (reset != 0 clears it after reading).  EMT_ERR_BAD_STATE if the
+ * histogram is off. */
+emt_status emt_read_step_hist(emt_ctx* ctx, uint64_t* out, int32_t bins, int32_t reset);
 
 /* Per-event results: summary = {edep, escaped, killed, e_in, n_steps,
  * n_tracks} (MeV, MeV, MeV, MeV, count, count); edep includes deposits in

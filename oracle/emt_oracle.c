@@ -443,7 +443,7 @@ struct orc_handle {
     int geom;      /* GEOM_LAYERS or GEOM_CYLINDERS */
     double half_z; /* cylinders: the stack spans |z| <= half_z */
     int score_z;   /* 1: histogram bins along z; 0: bins per volume */
-    double zs_lo, zs_w;
+    double zs_lo, zs_scale; /* z bin = floor((z - zs_lo) * zs_scale) */
     uint32_t seed;
 };
 
@@ -644,7 +644,7 @@ orc_handle* orc_create(const double* materials, int n_mat, const double* physics
     h->half_z = world[17];
     h->score_z = (int)world[18];
     h->zs_lo = world[19];
-    h->zs_w = (world[20] - world[19]) / (double)h->n_bins;
+    h->zs_scale = (double)h->n_bins / (world[20] - world[19]);
     if ((h->geom != 0 && h->geom != 1) || (h->geom == 1 && (h->zb[0] != 0.0 || !(h->half_z > 0.0))) ||
         (h->score_z && !(world[20] > world[19]))) {
         orc_destroy(h);
@@ -1273,12 +1273,13 @@ typedef struct {
 
 /* histogram bin of a deposit made in volume vol at height z: the
  * volume's score bin, or with scoring along z the bin of z among n_bins
- * equal bins of [zs_lo, zs_hi); -1 = no bin (the deposit still counts in
+ * equal bins of [zs_lo, zs_hi), floor((z - zs_lo) * n_bins / (zs_hi -
+ * zs_lo)) with the scale factor rounded once; -1 = no bin (the deposit still counts in
  * edep) */
 static int score_bin(const orc_handle* h, int vol, double z)
 {
     if (h->score_z) {
-        double f = floor((z - h->zs_lo) / h->zs_w);
+        double f = floor((z - h->zs_lo) * h->zs_scale);
         return (f >= 0.0 && f < (double)h->n_bins) ? (int)f : -1;
     }
     if (vol < 0) return -1;

@@ -36,13 +36,15 @@ struct Plan {
     }
     // tracks: [side][field]
     size_t trk[2][11];
-    size_t cnt, status, total_steps, done_head;
+    size_t cnt, status, total_steps, done_head, ehist;
     size_t hist, ledger, counts, live, event_id, done_ring;
     size_t grid, gridf, tab, tabf, dedx, mats, bk, vacuum, scratch;
     size_t zb, lmat, lbin;
     size_t st_ev, st_type, st_T, st_pos, st_dir, st_uid, st_slot, st_ids, st_start, st_runs;
     size_t slots_tmp, out_hist, out_summary;
     size_t iq[13];  // split schedule: interaction queue fields
+    size_t step_hist;  // [3][step_bins] when step_bins > 0
+    int step_bins;
     int64_t Q;
     int max_events, hstride, max_prim;
     bool mixed;
@@ -64,8 +66,9 @@ Plan make_plan(const emt_options& o)
         for (int f = 0; f < 11; ++f) p.trk[s][f] = p.add(Q * fs[f]);
     p.cnt = p.add(3 * sizeof(Counters));
     p.status = p.add(sizeof(int));
-    p.total_steps = p.add(2 * sizeof(unsigned long long));
+    p.total_steps = p.add(3 * sizeof(unsigned long long));
     p.done_head = p.add(sizeof(unsigned));
+    p.ehist = p.add(3 * kEBins * sizeof(unsigned));
     const size_t E = (size_t)p.max_events;
     p.hist = p.add(E * p.hstride * sizeof(double));
     p.ledger = p.add(E * 3 * sizeof(double));
@@ -107,6 +110,8 @@ Plan make_plan(const emt_options& o)
     }
     p.out_hist = p.add(E * (size_t)o.max_bins * sizeof(double));
     p.out_summary = p.add(E * EMT_SUMMARY_LEN * sizeof(double));
+    p.step_bins = o.step_hist_bins;
+    p.step_hist = p.step_bins > 0 ? p.add((size_t)3 * p.step_bins * sizeof(unsigned long long)) : 0;
     return p;
 }
 
@@ -122,7 +127,74 @@ bool valid_options(const emt_options& o, std::string& why)
     if (o.schedule != EMT_SCHEDULE_FUSED && o.schedule != EMT_SCHEDULE_SPLIT) return why = "schedule", false;
     if (o.loop_mode == EMT_LOOP_GRAPH && (o.graph_steps <= 0 || o.graph_steps % 6 != 0))
         return why = "graph_steps must be a positive multiple of 6", false;
+    if (o.step_hist_bins < 0 || o.step_hist_bins > (1 << 20)) return why = "step_hist_bins out of [0, 2^20]", false;
+    if (o.max_active < 0) return why = "max_active must be >= 0", false;
+    if (o.select_policy != EMT_SELECT_ORDER && o.select_policy != EMT_SELECT_LOW_ENERGY)
+        return why = "select_policy", false;
+    if (o.max_active > 0 && o.schedule != EMT_SCHEDULE_SPLIT)
+        return why = "track selection (max_active > 0) needs the split schedule", false;
     return true;
+}
+
+// Validate a geometry description and lay out its arrays: zb[n + 1] (plane
+// positions or shell radii), lm[n] (materials), lb[n] (score bins).
+// Returns an error message, or nullptr.
+const char* check_geometry(const emt_layer* layers, int n, const emt_world* w, int n_mat, int max_bins, double* zb,
+                           int* lm, int* lb)
+{
+    if (n < 1 || n > kMaxLayers) return "layer count out of [1, 4096]";
+    if (w->n_bins < 1 || w->n_bins > max_bins) return "n_bins out of [1, max_bins]";
+    if (w->max_steps < 1) return "max_steps";
+    if (w->geometry != EMT_GEOM_LAYERS && w->geometry != EMT_GEOM_CYLINDERS) return "geometry kind";
+    if (w->score_z != 0 && w->score_z != 1) return "score_z must be 0 or 1";
+    if (w->score_z && !(w->score_z_hi_cm > w->score_z_lo_cm)) return "score_z range must be non-empty";
+    zb[0] = w->z0_cm;
+    for (int i = 0; i < n; ++i) {
+        if (!(layers[i].thickness_cm > 0.0)) return "layer thickness must be positive";
+        if (layers[i].material < -1 || layers[i].material >= n_mat) return "layer material index";
+        zb[i + 1] = zb[i] + layers[i].thickness_cm;
+        lm[i] = layers[i].material;
+        lb[i] = layers[i].score_bin;
+    }
+    if (w->geometry == EMT_GEOM_LAYERS) {
+        if (!(w->half_x_cm > 0.0) || !(w->half_y_cm > 0.0)) return "stack half widths";
+        const double lo[3] = {-w->half_x_cm, -w->half_y_cm, zb[0]};
+        const double hi[3] = {w->half_x_cm, w->half_y_cm, zb[n]};
+        for (int a = 0; a < 3; ++a)
+            if (!(w->lo_cm[a] <= lo[a]) || !(w->hi_cm[a] >= hi[a])) return "the world box must contain the layer stack";
+    } else {
+        if (w->z0_cm != 0.0) return "cylinders: z0 (the innermost radius) must be 0";
+        if (!(w->half_z_cm > 0.0)) return "cylinders: half_z must be positive";
+    }
+    const double b2 = w->B_tesla[0] * w->B_tesla[0] + w->B_tesla[1] * w->B_tesla[1] + w->B_tesla[2] * w->B_tesla[2];
+    if (b2 > 0.0 && (!(w->rk_delta_cm > 0.0) || !(w->max_field_step_cm > 0.0)))
+        return "field needs rk_delta_cm > 0 and max_field_step_cm > 0";
+    return nullptr;
+}
+
+// geometry, field and scoring fields of the kernel parameters
+template <typename R>
+void set_geometry(Params<R>& p, int n, const emt_world* w)
+{
+    p.geom = w->geometry;
+    p.half_z = w->half_z_cm;
+    p.n_layers = n;
+    p.hx = w->half_x_cm;
+    p.hy = w->half_y_cm;
+    for (int a = 0; a < 3; ++a) {
+        p.wlo[a] = w->lo_cm[a];
+        p.whi[a] = w->hi_cm[a];
+        p.B[a] = w->B_tesla[a];
+    }
+    p.bmag = std::sqrt(w->B_tesla[0] * w->B_tesla[0] + w->B_tesla[1] * w->B_tesla[1] + w->B_tesla[2] * w->B_tesla[2]);
+    p.rk_delta = w->rk_delta_cm;
+    p.max_field_step = w->max_field_step_cm;
+    p.has_field = p.bmag > 0.0 ? 1 : 0;
+    p.max_steps = w->max_steps;
+    p.n_bins = w->n_bins;
+    p.score_z = w->score_z;
+    p.zs_lo = w->score_z_lo_cm;
+    p.zs_scale = w->score_z ? (double)w->n_bins / (w->score_z_hi_cm - w->score_z_lo_cm) : 1.0;
 }
 
 }  // namespace
@@ -153,7 +225,7 @@ struct emt_ctx {
     std::vector<int> order;  // slots in submission order
     unsigned done_seen = 0;
     // host mirrors valid while no device work has run since they were read
-    unsigned long long steps_seen[2] = {0, 0};  // total step counters
+    unsigned long long steps_seen[3] = {0, 0, 0};  // total step, deferred and held counters
     unsigned head_cached = 0;                    // finished-event ring head
     bool head_fresh = false;
     // pinned host mirrors
@@ -165,6 +237,9 @@ struct emt_ctx {
     // CUDA graph of graph_steps iterations
     cudaGraphExec_t graph = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // per-step records of emt_run_traced (null otherwise)
+    emt_step_record* trace = nullptr;
+    int32_t trace_cap = 0, trace_n = 0;
 
     template <typename T>
     T* at(size_t off) const { return reinterpret_cast<T*>(pool + off); }
@@ -254,6 +329,11 @@ void fill_common(emt_ctx* c, Params<R>& p)
     p.zb = c->at<double>(pl.zb);
     p.lmat = c->at<int>(pl.lmat);
     p.lbin = c->at<int>(pl.lbin);
+    p.step_bins = pl.step_bins;
+    p.step_hist = pl.step_bins > 0 ? c->at<unsigned long long>(pl.step_hist) : nullptr;
+    p.max_active = c->opt.max_active;
+    p.select_policy = c->opt.select_policy;
+    p.ehist = c->at<unsigned>(pl.ehist);
 }
 
 void drop_graph(emt_ctx* c)
@@ -375,11 +455,13 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
     std::memset(&s, 0, sizeof s);
     const Plan& pl = c->plan;
     c->head_fresh = false;
-    const unsigned long long steps0 = c->steps_seen[0], def0 = c->steps_seen[1];
+    const unsigned long long steps0 = c->steps_seen[0], def0 = c->steps_seen[1], held0 = c->steps_seen[2];
     unsigned long long last_steps = steps0;
     const int64_t live0 = c->live_g + c->live_c;
     int64_t peak = live0;
     double kernel_ms = 0.0;
+    unsigned long long deferred_prev = def0, held_prev = held0;
+    Counters trace_cnt[3];
     auto read_counts = [&]() -> emt_status {
         EMT_CUDA(c, cudaMemcpyAsync(c->h_cnt, c->pool + pl.cnt + sizeof(Counters) * (c->it % 3), sizeof(Counters),
                                     cudaMemcpyDeviceToHost, c->stream));
@@ -419,11 +501,29 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
         s.kernel_launches += c->plan.split ? 2 : 1;
         c->it += 1;
         s.iterations += 1;
-        return read_counts();
+        const int64_t g0 = c->live_g, c0 = c->live_c;
+        const double ms0 = kernel_ms;
+        emt_status r = read_counts();
+        if (r != EMT_OK || !c->trace || c->trace_n >= c->trace_cap) return r;
+        // per-step record: the input counters of this step hold its
+        // interaction count; the step counters give the deferred copies
+        EMT_CUDA(c, cudaMemcpyAsync(trace_cnt, c->pool + pl.cnt, sizeof trace_cnt, cudaMemcpyDeviceToHost, c->stream));
+        EMT_CUDA(c, cudaMemcpyAsync(c->h_steps, c->pool + pl.total_steps, 24, cudaMemcpyDeviceToHost, c->stream));
+        EMT_CUDA(c, cudaStreamSynchronize(c->stream));
+        emt_step_record& rec = c->trace[c->trace_n++];
+        rec.photons = g0;
+        rec.charged = c0;
+        rec.interacting = c->plan.split ? (int64_t)trace_cnt[cin].n_int : -1;
+        rec.deferred = (int64_t)(c->h_steps[1] - deferred_prev);
+        deferred_prev = c->h_steps[1];
+        rec.held = (int64_t)(c->h_steps[2] - held_prev);
+        held_prev = c->h_steps[2];
+        rec.ms = kernel_ms - ms0;
+        return EMT_OK;
     };
     int64_t done_it = 0;
     auto budget_left = [&]() { return max_iterations <= 0 || done_it < max_iterations; };
-    if (c->opt.loop_mode == EMT_LOOP_PLAIN) {
+    if (c->opt.loop_mode == EMT_LOOP_PLAIN || c->trace) {
         while (c->live_g + c->live_c > 0 && budget_left()) {
             emt_status r = one_plain();
             if (r != EMT_OK) return r;
@@ -475,6 +575,7 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
     const unsigned long long* steps = reinterpret_cast<const unsigned long long*>(c->h_misc + (pl.total_steps - pl.status));
     c->steps_seen[0] = steps[0];
     c->steps_seen[1] = steps[1];
+    c->steps_seen[2] = steps[2];
     c->head_cached = *reinterpret_cast<const unsigned*>(c->h_misc + (pl.done_head - pl.status));
     c->head_fresh = true;
     if (status & (int)kStatusQueueOverflow) {
@@ -483,12 +584,13 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
     }
     s.track_steps = (int64_t)(c->steps_seen[0] - steps0);
     s.deferred = (int64_t)(c->steps_seen[1] - def0);
+    s.held = (int64_t)(c->steps_seen[2] - held0);
     s.peak_tracks = peak;
     s.live_tracks = c->live_g + c->live_c;
     s.kernel_ms = kernel_ms;
     // every launch reads its inputs and writes its outputs once; the
     // outputs of one launch are the inputs of the next
-    const int64_t n_in = s.track_steps + s.deferred;
+    const int64_t n_in = s.track_steps + s.deferred + s.held;
     const int64_t slot_bytes = c->mixed() ? 60 : 76;
     s.state_bytes = (2 * n_in - live0 + s.live_tracks) * slot_bytes;
     if (st) *st = s;
@@ -597,7 +699,7 @@ emt_status emt_create(const emt_options* o, emt_ctx** out)
     }
     if (cudaMallocHost((void**)&c->h_cnt, sizeof(Counters)) != cudaSuccess ||
         cudaMallocHost((void**)&c->h_status, sizeof(int)) != cudaSuccess ||
-        cudaMallocHost((void**)&c->h_steps, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost((void**)&c->h_steps, 3 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost((void**)&c->h_done, sizeof(unsigned)) != cudaSuccess ||
         cudaMallocHost((void**)&c->h_misc, make_plan(*o).done_head + sizeof(unsigned) - make_plan(*o).status) !=
             cudaSuccess)
@@ -607,6 +709,10 @@ emt_status emt_create(const emt_options* o, emt_ctx** out)
     // counters, status and score metadata start at zero
     if (cudaMemsetAsync(c->pool + pl.cnt, 0, pl.hist - pl.cnt, c->stream) != cudaSuccess) return bail(EMT_ERR_CUDA);
     if (cudaMemsetAsync(c->pool + pl.live, 0, pl.grid - pl.live, c->stream) != cudaSuccess) return bail(EMT_ERR_CUDA);
+    if (pl.step_bins > 0 &&
+        cudaMemsetAsync(c->pool + pl.step_hist, 0, (size_t)3 * pl.step_bins * sizeof(unsigned long long), c->stream) !=
+            cudaSuccess)
+        return bail(EMT_ERR_CUDA);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(EMT_ERR_CUDA);
     fill_common(c, c->pd);
     fill_common(c, c->pf);
@@ -726,53 +832,18 @@ emt_status emt_load_geometry(emt_ctx* c, const emt_layer* layers, int32_t n, con
     if (c->poisoned) return fail(c, EMT_ERR_CUDA, "context unusable");
     if (!c->have_materials) return fail(c, EMT_ERR_BAD_STATE, "load materials first");
     if (n < 1 || n > kMaxLayers) return fail(c, EMT_ERR_INVALID_ARG, "layer count out of [1, 4096]");
-    if (w->n_bins < 1 || w->n_bins > c->opt.max_bins) return fail(c, EMT_ERR_INVALID_ARG, "n_bins out of [1, max_bins]");
-    if (!(w->half_x_cm > 0.0) || !(w->half_y_cm > 0.0)) return fail(c, EMT_ERR_INVALID_ARG, "stack half widths");
-    if (w->max_steps < 1) return fail(c, EMT_ERR_INVALID_ARG, "max_steps");
     std::vector<double> zb(n + 1);
     std::vector<int> lm(n), lb(n);
-    zb[0] = w->z0_cm;
-    for (int i = 0; i < n; ++i) {
-        if (!(layers[i].thickness_cm > 0.0)) return fail(c, EMT_ERR_INVALID_ARG, "layer thickness must be positive");
-        if (layers[i].material < -1 || layers[i].material >= c->n_mat)
-            return fail(c, EMT_ERR_INVALID_ARG, "layer material index");
-        zb[i + 1] = zb[i] + layers[i].thickness_cm;
-        lm[i] = layers[i].material;
-        lb[i] = layers[i].score_bin;
-    }
-    const double lo[3] = {-w->half_x_cm, -w->half_y_cm, zb[0]};
-    const double hi[3] = {w->half_x_cm, w->half_y_cm, zb[n]};
-    for (int a = 0; a < 3; ++a)
-        if (!(w->lo_cm[a] <= lo[a]) || !(w->hi_cm[a] >= hi[a]))
-            return fail(c, EMT_ERR_INVALID_ARG, "the world box must contain the layer stack");
-    double bmag = std::sqrt(w->B_tesla[0] * w->B_tesla[0] + w->B_tesla[1] * w->B_tesla[1] + w->B_tesla[2] * w->B_tesla[2]);
-    bool field = bmag > 0.0;
-    if (field && (!(w->rk_delta_cm > 0.0) || !(w->max_field_step_cm > 0.0)))
-        return fail(c, EMT_ERR_INVALID_ARG, "field needs rk_delta_cm > 0 and max_field_step_cm > 0");
+    if (const char* why = check_geometry(layers, n, w, c->n_mat, c->opt.max_bins, zb.data(), lm.data(), lb.data()))
+        return fail(c, EMT_ERR_INVALID_ARG, why);
     if (cudaSetDevice(c->opt.device) != cudaSuccess) return fail(c, EMT_ERR_CUDA, "cudaSetDevice");
     const Plan& pl = c->plan;
     EMT_CUDA(c, cudaMemcpyAsync(c->pool + pl.zb, zb.data(), sizeof(double) * (n + 1), cudaMemcpyHostToDevice, c->stream));
     EMT_CUDA(c, cudaMemcpyAsync(c->pool + pl.lmat, lm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->stream));
     EMT_CUDA(c, cudaMemcpyAsync(c->pool + pl.lbin, lb.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->stream));
     EMT_CUDA(c, cudaStreamSynchronize(c->stream));
-    auto setg = [&](auto& p) {
-        p.n_layers = n;
-        p.hx = w->half_x_cm;
-        p.hy = w->half_y_cm;
-        for (int a = 0; a < 3; ++a) {
-            p.wlo[a] = w->lo_cm[a];
-            p.whi[a] = w->hi_cm[a];
-            p.B[a] = w->B_tesla[a];
-        }
-        p.bmag = bmag;
-        p.rk_delta = w->rk_delta_cm;
-        p.max_field_step = w->max_field_step_cm;
-        p.has_field = field ? 1 : 0;
-        p.max_steps = w->max_steps;
-        p.n_bins = w->n_bins;
-    };
-    setg(c->pd);
-    setg(c->pf);
+    set_geometry(c->pd, n, w);
+    set_geometry(c->pf, n, w);
     c->n_layers = n;
     c->n_bins = w->n_bins;
     drop_graph(c);
@@ -911,6 +982,37 @@ emt_status emt_run(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
     r = c->mixed() ? run_loop<float>(c, max_iterations, st) : run_loop<double>(c, max_iterations, st);
     if (r != EMT_OK) return r;
     return drain_done(c);
+}
+
+emt_status emt_run_traced(emt_ctx* c, int32_t max_iterations, emt_run_stats* st, emt_step_record* rec, int32_t cap,
+                          int32_t* n_rec)
+{
+    emt_status r = check_ready(c);
+    if (r != EMT_OK) return r;
+    if (!n_rec || cap < 0 || (cap > 0 && !rec)) return fail(c, EMT_ERR_INVALID_ARG, "trace buffer");
+    c->trace = rec;
+    c->trace_cap = cap;
+    c->trace_n = 0;
+    r = c->mixed() ? run_loop<float>(c, max_iterations, st) : run_loop<double>(c, max_iterations, st);
+    *n_rec = c->trace_n;
+    c->trace = nullptr;
+    c->trace_cap = c->trace_n = 0;
+    if (r != EMT_OK) return r;
+    return drain_done(c);
+}
+
+emt_status emt_read_step_hist(emt_ctx* c, uint64_t* out, int32_t bins, int32_t reset)
+{
+    if (!c) return EMT_ERR_INVALID_ARG;
+    if (c->poisoned) return fail(c, EMT_ERR_CUDA, "context unusable after an earlier CUDA error");
+    if (c->plan.step_bins <= 0) return fail(c, EMT_ERR_BAD_STATE, "the steps-per-track histogram is off");
+    if (!out || bins != c->plan.step_bins) return fail(c, EMT_ERR_INVALID_ARG, "bins must equal step_hist_bins");
+    if (cudaSetDevice(c->opt.device) != cudaSuccess) return fail(c, EMT_ERR_CUDA, "cudaSetDevice");
+    const size_t bytes = (size_t)3 * bins * sizeof(unsigned long long);
+    EMT_CUDA(c, cudaMemcpyAsync(out, c->pool + c->plan.step_hist, bytes, cudaMemcpyDeviceToHost, c->stream));
+    if (reset) EMT_CUDA(c, cudaMemsetAsync(c->pool + c->plan.step_hist, 0, bytes, c->stream));
+    EMT_CUDA(c, cudaStreamSynchronize(c->stream));
+    return EMT_OK;
 }
 
 emt_status emt_poll(emt_ctx* c, uint64_t* done_ids, int32_t cap, int32_t* n_done)
@@ -1150,7 +1252,6 @@ extern "C" emt_status emt_transport_static(int32_t device, uint32_t seed, const 
     for (int k = 0; k < 3; ++k)
         if (!(ph->cut_MeV[k] > 0.0)) return EMT_ERR_INVALID_ARG;
     if (!(ph->step_frac > 0.0) || !(ph->final_range_cm > 0.0) || w->max_steps < 1) return EMT_ERR_INVALID_ARG;
-    if (!(w->half_x_cm > 0.0) || !(w->half_y_cm > 0.0)) return EMT_ERR_INVALID_ARG;
     for (int e = 0; e < n_events; ++e)
         for (int f = e + 1; f < n_events; ++f)
             if (event_ids[e] == event_ids[f]) return EMT_ERR_INVALID_ARG;
@@ -1234,39 +1335,12 @@ extern "C" emt_status emt_transport_static(int32_t device, uint32_t seed, const 
     // ---- geometry
     double zb[kMaxLayers + 1];
     int lm[kMaxLayers], lb[kMaxLayers];
-    zb[0] = w->z0_cm;
-    for (int i = 0; i < n_layers; ++i) {
-        if (!(layers[i].thickness_cm > 0.0) || layers[i].material < -1 || layers[i].material >= n_mat)
-            return EMT_ERR_INVALID_ARG;
-        zb[i + 1] = zb[i] + layers[i].thickness_cm;
-        lm[i] = layers[i].material;
-        lb[i] = layers[i].score_bin;
-    }
-    const double glo[3] = {-w->half_x_cm, -w->half_y_cm, zb[0]};
-    const double ghi[3] = {w->half_x_cm, w->half_y_cm, zb[n_layers]};
-    for (int a = 0; a < 3; ++a)
-        if (!(w->lo_cm[a] <= glo[a]) || !(w->hi_cm[a] >= ghi[a])) return EMT_ERR_INVALID_ARG;
-    const double bmag =
-        std::sqrt(w->B_tesla[0] * w->B_tesla[0] + w->B_tesla[1] * w->B_tesla[1] + w->B_tesla[2] * w->B_tesla[2]);
-    if (bmag > 0.0 && (!(w->rk_delta_cm > 0.0) || !(w->max_field_step_cm > 0.0))) return EMT_ERR_INVALID_ARG;
+    if (check_geometry(layers, n_layers, w, n_mat, EMT_STATIC_MAX_BINS, zb, lm, lb)) return EMT_ERR_INVALID_ARG;
     if (cudaMemcpyAsync(pool + pl.zb, zb, sizeof(double) * (n_layers + 1), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(pool + pl.lmat, lm, sizeof(int) * n_layers, cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(pool + pl.lbin, lb, sizeof(int) * n_layers, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return EMT_ERR_CUDA;
-    p.n_layers = n_layers;
-    p.hx = w->half_x_cm;
-    p.hy = w->half_y_cm;
-    for (int a = 0; a < 3; ++a) {
-        p.wlo[a] = w->lo_cm[a];
-        p.whi[a] = w->hi_cm[a];
-        p.B[a] = w->B_tesla[a];
-    }
-    p.bmag = bmag;
-    p.rk_delta = w->rk_delta_cm;
-    p.max_field_step = w->max_field_step_cm;
-    p.has_field = bmag > 0.0 ? 1 : 0;
-    p.max_steps = w->max_steps;
-    p.n_bins = w->n_bins;
+    set_geometry(p, n_layers, w);
 
     // ---- events: slots 0..n_events-1 in order; primaries read in place
     uint32_t slots[EMT_STATIC_MAX_EVENTS];

@@ -26,12 +26,19 @@ constexpr int kMaxMat = 16;
 constexpr int kMaxLayers = 4096;
 constexpr int kVolWorld = -1;               // vacuum of the world box
 constexpr int kVolOut = -2;                 // left the world
+constexpr int kGeomLayers = 0;              // slabs stacked along z in a world box
+constexpr int kGeomCylinders = 1;           // concentric shells about the z axis
 constexpr int kNq = 4;                      // table quantities per node
 // Rejection loops accept their candidate after kMaxTrials trials: a bound
 // against non-finite input (every acceptance probability is >= 1/3).
 constexpr int kMaxTrials = 1000;
 
 // status bits written by kernels (host reads after each run)
+// track selection (active budget per step)
+constexpr int kSelectOrder = 0;      // the first max_active tracks of the input order
+constexpr int kSelectLowEnergy = 1;  // the max_active tracks of lowest energy
+constexpr int kEBins = 128;          // energy classes: quarter octaves from 2^-16 MeV
+constexpr int kEBase = 112 << 2;     // (FP32 exponent << 2 | two mantissa bits) of class 0
 constexpr int kStatusQueueOverflow = 1;
 constexpr int kStatusBadTrack = 2;
 
@@ -104,7 +111,8 @@ struct Counters {
     int used;      // growth tokens taken (steps with two outputs)
     int n_int;     // split schedule: tracks queued for an interaction
     int work_b;    // split schedule: chunk dispenser of the interaction kernel
-    int pad[2];
+    int ticket;    // track selection: tickets of the boundary energy class
+    int pad;
 };
 
 // Split schedule: tracks that interact in a step, queued by the transport
@@ -140,7 +148,10 @@ struct Params {
     double step_frac, final_range;
     float cutf[3];  // the same in FP32 (mixed path)
     float step_fracf, final_rangef;
-    // geometry
+    // geometry: layers (zb = plane positions) or cylinders (zb = shell
+    // radii, zb[0] = 0, the stack spans |z| <= half_z)
+    int geom;
+    double half_z;
     const double* zb;
     const int* lmat;
     const int* lbin;
@@ -156,13 +167,17 @@ struct Params {
     double* hist;  // [slot][hstride]; column n_bins collects unbinned deposits
     int hstride;
     int n_bins;
+    int score_z;           // bins along z: floor((z - zs_lo) * zs_scale); else per volume
+    double zs_lo, zs_scale;
+    unsigned long long* step_hist;  // [3][step_bins] steps per finished track, or null
+    int step_bins;
     double* ledger;                 // [slot][3] escaped, killed, e_in
     unsigned long long* counts;     // [slot][2] steps, tracks
     const uint64_t* event_id;       // [slot]
     int* live;                      // [slot] tracks alive (+1 submission token)
     unsigned* done_ring;            // [max_events] slots of finished events
     unsigned* done_head;            // total finished events (ring index)
-    unsigned long long* total_steps;  // [0] track-steps taken, [1] deferred copies
+    unsigned long long* total_steps;  // [0] track-steps taken, [1] deferred copies, [2] held copies
     int max_events;
     uint32_t seed;
     // queues
@@ -171,7 +186,22 @@ struct Params {
     Counters* cnt;  // [3]
     int* status;
     InterQueue<R> iq;  // split schedule only
+    // track selection: at most max_active tracks step per iteration (0 =
+    // all), chosen by select_policy; the others are held (copied
+    // unchanged).  ehist[3][kEBins]: energy classes of each counter slot's
+    // tracks (rotating with the counters).
+    long long max_active;
+    int select_policy;
+    unsigned* ehist;
 };
+
+// energy class of a kinetic energy (monotonic in T): the FP32 exponent and
+// two leading mantissa bits, offset and clamped to [0, kEBins)
+__device__ __forceinline__ int energy_class(float T)
+{
+    const int c = (int)(__float_as_uint(T) >> 21) - kEBase;
+    return c < 0 ? 0 : (c >= kEBins ? kEBins - 1 : c);
+}
 
 // production cut of particle type t and the e+- step-limit constants in R
 template <typename R>
@@ -413,11 +443,114 @@ __device__ __forceinline__ int layer_at(const double* zb, int L, double z)
     return lo;
 }
 
+// Cylinders: exit parameter t >= 0 along d (any length) from x in shell
+// vol.  Candidates in the order end plane, outer surface, inner surface;
+// the smallest wins, ties to the earlier.  The surface rho = r meets
+// x + t d where a t^2 + 2 b t + c = 0 (a = dx^2 + dy^2, b = x dx + y dy,
+// c = x^2 + y^2 - r^2).  Outer surface: the larger root, in the form free
+// of cancellation for the sign of b; inner surface: only moving inward
+// (b < 0) with a non-negative discriminant, the smaller root.  A radial
+// crossing moves to the neighbouring shell; the end planes and the
+// outermost surface lead out of the world (no snapping onto a curved
+// surface: the volume index is exact, the position is the computed one).
+template <typename R>
+__device__ __forceinline__ Exit nav_exit_cyl(const Params<R>& p, int vol, const double x[3], const double d[3])
+{
+    Exit e;
+    e.t = __longlong_as_double(0x7FF0000000000000ll);
+    e.next = kVolOut;
+    e.axis = -1;
+    e.plane = 0.0;
+    if (d[2] != 0.0) {
+        const double pl = d[2] > 0.0 ? p.half_z : -p.half_z;
+        e.t = (pl - x[2]) / d[2];
+        e.axis = 2;
+        e.plane = pl;
+    }
+    const double a = d[0] * d[0] + d[1] * d[1];
+    if (a > 0.0) {
+        const double b = x[0] * d[0] + x[1] * d[1];
+        const double q = x[0] * x[0] + x[1] * x[1];
+        const double ro = p.zb[vol + 1];
+        const double c = q - ro * ro;
+        double disc = b * b - a * c;
+        if (disc < 0.0) disc = 0.0;
+        const double sq = sqrt(disc);
+        const double t = b > 0.0 ? -c / (b + sq) : (sq - b) / a;
+        if (t < e.t) {
+            e.t = t;
+            e.axis = -1;
+            e.plane = 0.0;
+            e.next = vol + 1 < p.n_layers ? vol + 1 : kVolOut;
+        }
+        if (vol > 0 && b < 0.0) {
+            const double ri = p.zb[vol];
+            const double ci = q - ri * ri;
+            const double di = b * b - a * ci;
+            if (di >= 0.0) {
+                const double ti = ci / (sqrt(di) - b);
+                if (ti < e.t) {
+                    e.t = ti;
+                    e.axis = -1;
+                    e.plane = 0.0;
+                    e.next = vol - 1;
+                }
+            }
+        }
+    }
+    if (e.t < 0.0) e.t = 0.0;
+    return e;
+}
+
+// logical volume of a starting point (primaries): the layer (or shell)
+// containing it, the world vacuum, or kVolOut
+template <typename R>
+__device__ __forceinline__ int locate_volume(const Params<R>& p, const double x[3])
+{
+    if (p.geom == kGeomCylinders) {
+        const double q = x[0] * x[0] + x[1] * x[1];
+        const double rmax = p.zb[p.n_layers];
+        if (!(x[2] >= -p.half_z && x[2] <= p.half_z) || !(q < rmax * rmax)) return kVolOut;
+        int lo = 0, hi = p.n_layers - 1;  // largest j with zb[j]^2 <= q
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (p.zb[mid] * p.zb[mid] <= q)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        return lo;
+    }
+    if (x[0] >= -p.hx && x[0] <= p.hx && x[1] >= -p.hy && x[1] <= p.hy && x[2] >= p.zb[0] &&
+        x[2] <= p.zb[p.n_layers])
+        return layer_at(p.zb, p.n_layers, x[2]);
+    if (x[0] < p.wlo[0] || x[0] > p.whi[0] || x[1] < p.wlo[1] || x[1] > p.whi[1] || x[2] < p.wlo[2] ||
+        x[2] > p.whi[2])
+        return kVolOut;
+    return kVolWorld;
+}
+
+// histogram column of a deposit in volume vol at height z (column n_bins
+// collects deposits outside every bin)
+template <typename R>
+__device__ __forceinline__ int score_col(const Params<R>& p, int vol, double z)
+{
+    if (p.score_z) {
+        const double f = floor((z - p.zs_lo) * p.zs_scale);
+        return (f >= 0.0 && f < (double)p.n_bins) ? (int)f : p.n_bins;
+    }
+    if (vol >= 0) {
+        const int b = p.lbin[vol];
+        if (b >= 0 && b < p.n_bins) return b;
+    }
+    return p.n_bins;
+}
+
 // exit parameter t >= 0 along d (any length) from point x in volume vol.
 // Layer: z plane first, then the x and y walls; ties keep the earlier.
 // World vacuum: stack faces (z, x, y) first, then the world walls.
 template <typename R>
-__device__ __forceinline__ Exit nav_exit(const Params<R>& p, int vol, const double x[3], const double d[3])
+__device__ __forceinline__ Exit nav_exit_layers(const Params<R>& p, int vol, const double x[3], const double d[3])
 {
     Exit e;
     e.t = __longlong_as_double(0x7FF0000000000000ll);
@@ -524,6 +657,16 @@ __device__ __forceinline__ Exit nav_exit(const Params<R>& p, int vol, const doub
     return e;
 }
 
+// the exit of geometry kind G (kernels are instantiated per kind)
+template <int G, typename R>
+__device__ __forceinline__ Exit nav_exit(const Params<R>& p, int vol, const double x[3], const double d[3])
+{
+    if constexpr (G == kGeomCylinders)
+        return nav_exit_cyl(p, vol, x, d);
+    else
+        return nav_exit_layers(p, vol, x, d);
+}
+
 // ------------------------------------------------------------------ field
 // classical RK4 in path length on (x, u), du/ds = kq u x B, |p| fixed
 // during the step; u renormalised after each substep.  The direction and
@@ -568,8 +711,9 @@ __device__ __forceinline__ void rk4(const Params<R>& p, R kq, const double x[3],
 // x1 lies inside the volume by more than kChordMargin, and in the world
 // vacuum the chord's bounding box also stays kChordMargin away from the
 // layer stack.  nav_exit would then return t > 1 for this chord (the exact
-// exit parameter exceeds 1 by at least margin/|c|, far above rounding), so
-// skipping it changes no result.
+// exit parameter exceeds 1 by at least margin/|c|, far above rounding), and
+// for a straight step to x1 = x + s u (unit u) an exit distance above s by
+// at least the margin, so skipping it changes no result.
 constexpr double kChordMargin = 1e-6;  // cm
 
 // A step in a field takes at most kMaxSubsteps substeps of h_max (and at
@@ -577,10 +721,33 @@ constexpr double kChordMargin = 1e-6;  // cm
 // interaction: it bounds the work of one step of a looping track.
 constexpr int kMaxSubsteps = 100;
 
-template <typename R>
+// Cylinders: both ends within the shell's end planes and inside the circle
+// of radius r_out - margin (the disc is convex, so the whole chord is), and
+// for a hollow shell every point of the chord outside r_in + margin (both
+// ends, and the chord's closest approach to the axis when it lies between
+// them).  The exit parameter of the quadratic is then > 1 by at least
+// margin/|c|, while its rounding error is below 1e-9/|c| for radii up to
+// several metres (the discriminant is at least a * 2 r margin).
+template <int G, typename R>
 __device__ __forceinline__ bool chord_inside(const Params<R>& p, int vol, const double x[3], const double x1[3])
 {
     const double m = kChordMargin;
+    if constexpr (G == kGeomCylinders) {
+        if (!(x1[2] > -p.half_z + m && x1[2] < p.half_z - m)) return false;
+        const double ro = p.zb[vol + 1] - m;
+        const double q1 = x1[0] * x1[0] + x1[1] * x1[1];
+        if (!(q1 < ro * ro)) return false;
+        if (vol > 0) {
+            const double ri = p.zb[vol] + m;
+            const double ri2 = ri * ri;
+            const double q0 = x[0] * x[0] + x[1] * x[1];
+            if (!(q1 > ri2) || !(q0 > ri2)) return false;
+            const double cx = x1[0] - x[0], cy = x1[1] - x[1];
+            const double a = cx * cx + cy * cy, b = x[0] * cx + x[1] * cy;
+            if (b < 0.0 && -b < a && !(q0 - b * (b / a) > ri2)) return false;
+        }
+        return true;
+    }
     if (vol >= 0) {
         return x1[2] > p.zb[vol] + m && x1[2] < p.zb[vol + 1] - m && x1[0] > -p.hx + m && x1[0] < p.hx - m &&
                x1[1] > -p.hy + m && x1[1] < p.hy - m;
@@ -603,7 +770,7 @@ __device__ __forceinline__ bool chord_inside(const Params<R>& p, int vol, const 
 // the chord of each substep is tested against the current volume and a
 // crossing at fraction f repeats the substep with h f, snapped onto the
 // plane.  Returns the path length.
-template <typename R>
+template <int G, typename R>
 __device__ __forceinline__ double propagate_field(const Params<R>& p, int charge, double T, int vol, double x[3],
                                                   R u[3], double smax, Exit* bnd, bool* crossed)
 {
@@ -621,14 +788,14 @@ __device__ __forceinline__ double propagate_field(const Params<R>& p, int charge
         double x1[3], c[3];
         R u1[3];
         rk4(p, R(kq), x, u, R(hs), x1, u1);
-        if (!chord_inside(p, vol, x, x1)) {
+        if (!chord_inside<G>(p, vol, x, x1)) {
 #pragma unroll
             for (int a = 0; a < 3; ++a) c[a] = x1[a] - x[a];
-            Exit e = nav_exit(p, vol, x, c);
+            Exit e = nav_exit<G>(p, vol, x, c);
             if (e.t <= 1.0) {
                 double h2 = hs * e.t;
                 rk4(p, R(kq), x, u, R(h2), x1, u1);
-                x1[e.axis] = e.plane;
+                if (e.axis >= 0) x1[e.axis] = e.plane;
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     x[a] = x1[a];

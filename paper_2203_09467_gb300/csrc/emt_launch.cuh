@@ -11,12 +11,20 @@ template <typename R>
 cudaError_t Launch<R>::step(const Params<R>& p, int side, int cin, int cout, int cclr, int grid, int block,
                             cudaStream_t st)
 {
-    if (block == 128)
-        k_step<R, 128><<<grid, 128, 0, st>>>(p, side, cin, cout, cclr);
-    else if (block == 256)
-        k_step<R, 256><<<grid, 256, 0, st>>>(p, side, cin, cout, cclr);
-    else
+    const bool cyl = p.geom == kGeomCylinders;
+    if (block == 128) {
+        if (cyl)
+            k_step<R, 128, kGeomCylinders><<<grid, 128, 0, st>>>(p, side, cin, cout, cclr);
+        else
+            k_step<R, 128, kGeomLayers><<<grid, 128, 0, st>>>(p, side, cin, cout, cclr);
+    } else if (block == 256) {
+        if (cyl)
+            k_step<R, 256, kGeomCylinders><<<grid, 256, 0, st>>>(p, side, cin, cout, cclr);
+        else
+            k_step<R, 256, kGeomLayers><<<grid, 256, 0, st>>>(p, side, cin, cout, cclr);
+    } else {
         return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
@@ -49,13 +57,21 @@ cudaError_t Launch<R>::get_tracks(const Params<R>& p, int side, int nG, int nC, 
     return cudaGetLastError();
 }
 
+// resident blocks per SM, the smaller of the two geometry instantiations
 template <typename R>
 int Launch<R>::max_blocks_per_sm(int block)
 {
-    int n = 0;
-    cudaError_t e = block == 128 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<R, 128>, 128, 0)
-                                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<R, 256>, 256, 0);
-    if (e != cudaSuccess) return 1;
+    int n1 = 0, n2 = 0;
+    cudaError_t e1, e2;
+    if (block == 128) {
+        e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_step<R, 128, kGeomLayers>, 128, 0);
+        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, k_step<R, 128, kGeomCylinders>, 128, 0);
+    } else {
+        e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_step<R, 256, kGeomLayers>, 256, 0);
+        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, k_step<R, 256, kGeomCylinders>, 256, 0);
+    }
+    if (e1 != cudaSuccess || e2 != cudaSuccess) return 1;
+    const int n = n1 < n2 ? n1 : n2;
     return n > 0 ? n : 1;
 }
 
@@ -65,35 +81,68 @@ int Launch<R>::max_blocks_per_sm(int block)
 
 namespace emt {
 
+template <typename R, int BS, bool S>
+static void launch_split(const Params<R>& p, int side, int cin, int cout, int cclr, int grid_a, int grid_b,
+                         cudaStream_t st)
+{
+    if (p.geom == kGeomCylinders)
+        k_transport<R, BS, kGeomCylinders, S><<<grid_a, BS, 0, st>>>(p, side, cin, cout, cclr);
+    else
+        k_transport<R, BS, kGeomLayers, S><<<grid_a, BS, 0, st>>>(p, side, cin, cout, cclr);
+    k_interact<R, BS, S><<<grid_b, BS, 0, st>>>(p, side, cin, cout);
+}
+
 template <typename R>
 cudaError_t Launch<R>::step_split(const Params<R>& p, int side, int cin, int cout, int cclr, int grid_a, int grid_b,
                                   int block, cudaStream_t st)
 {
+    const bool sel = p.max_active > 0;
     if (block == 128) {
-        k_transport<R, 128><<<grid_a, 128, 0, st>>>(p, side, cin, cout, cclr);
-        k_interact<R, 128><<<grid_b, 128, 0, st>>>(p, side, cin, cout);
+        if (sel)
+            launch_split<R, 128, true>(p, side, cin, cout, cclr, grid_a, grid_b, st);
+        else
+            launch_split<R, 128, false>(p, side, cin, cout, cclr, grid_a, grid_b, st);
     } else if (block == 256) {
-        k_transport<R, 256><<<grid_a, 256, 0, st>>>(p, side, cin, cout, cclr);
-        k_interact<R, 256><<<grid_b, 256, 0, st>>>(p, side, cin, cout);
+        if (sel)
+            launch_split<R, 256, true>(p, side, cin, cout, cclr, grid_a, grid_b, st);
+        else
+            launch_split<R, 256, false>(p, side, cin, cout, cclr, grid_a, grid_b, st);
     } else {
         return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
+// resident blocks per SM of the split kernels (which 0: transport, 1:
+// interaction), the smallest over the instantiations
+template <typename R, int BS>
+static int min_blocks_split(int which)
+{
+    int n[4] = {0, 0, 0, 0};
+    cudaError_t e[4];
+    if (which == 0) {
+        e[0] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[0], k_transport<R, BS, kGeomLayers, false>, BS, 0);
+        e[1] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[1], k_transport<R, BS, kGeomCylinders, false>, BS, 0);
+        e[2] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[2], k_transport<R, BS, kGeomLayers, true>, BS, 0);
+        e[3] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[3], k_transport<R, BS, kGeomCylinders, true>, BS, 0);
+    } else {
+        e[0] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[0], k_interact<R, BS, false>, BS, 0);
+        e[1] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[1], k_interact<R, BS, true>, BS, 0);
+        e[2] = e[3] = cudaSuccess;
+        n[2] = n[3] = n[0];
+    }
+    int m = 1 << 30;
+    for (int k = 0; k < 4; ++k) {
+        if (e[k] != cudaSuccess) return 1;
+        if (n[k] < m) m = n[k];
+    }
+    return m > 0 ? m : 1;
+}
+
 template <typename R>
 int Launch<R>::max_blocks_split(int block, int which)
 {
-    int n = 0;
-    cudaError_t e;
-    if (which == 0)
-        e = block == 128 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_transport<R, 128>, 128, 0)
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_transport<R, 256>, 256, 0);
-    else
-        e = block == 128 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_interact<R, 128>, 128, 0)
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_interact<R, 256>, 256, 0);
-    if (e != cudaSuccess) return 1;
-    return n > 0 ? n : 1;
+    return block == 128 ? min_blocks_split<R, 128>(which) : min_blocks_split<R, 256>(which);
 }
 
 }  // namespace emt

@@ -22,11 +22,33 @@ __device__ __forceinline__ uint32_t pack_tvm(int type, int vol, int model)
     return (uint32_t)type | ((uint32_t)(vol + 2) << 8) | ((uint32_t)model << 24);
 }
 
-template <typename R, int BS>
+// Track selection (max_active > 0): the tracks that do not fit the step's
+// budget are held, copied unchanged with their step counter, so they draw
+// the same random numbers when they do step and no result depends on the
+// policy; both kernels count their outputs' energy classes for the next
+// step's selection.
+template <typename R, int BS, int G, bool S>
 __global__ void __launch_bounds__(BS, 512 / BS) k_transport(Params<R> p, int side, int cin, int cout, int cclr)
 {
     __shared__ int s_chunk;
+    __shared__ unsigned s_eh[S ? kEBins : 1];
+    __shared__ Selection s_sel;
+    constexpr bool select = S;
     if (blockIdx.x == 0 && threadIdx.x == 0) p.cnt[cclr] = Counters{};
+    if constexpr (select) {
+        for (int b = threadIdx.x; b < kEBins; b += BS) {
+            s_eh[b] = 0u;
+            if (blockIdx.x == 0) p.ehist[(size_t)cclr * kEBins + b] = 0u;
+        }
+        if (threadIdx.x < 32) {
+            Selection sl;
+            sl.cls = kEBins;
+            sl.quota = 0;
+            if (p.select_policy == kSelectLowEnergy) sl = select_threshold(p, cin, threadIdx.x);
+            if (threadIdx.x == 0) s_sel = sl;
+        }
+        __syncthreads();
+    }
     const Tracks<R> qi = p.q[side];
     const Tracks<R> qo = p.q[side ^ 1];
     const int nG = p.cnt[cin].n[0];
@@ -57,20 +79,41 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_transport(Params<R> p, int sid
         StepOut<R> o;
         o.n = 0;
         int model = kNoInteraction;
-        if (active) {
-            load_track(qi, src, t);
+        bool held = false;
+        if (active) load_track(qi, src, t);
+        if constexpr (select) {
+            if (p.select_policy == kSelectOrder) {
+                held = active && (photon_chunk ? i : nG + i) >= p.max_active;
+            } else {
+                const int cls = active ? energy_class(est_f(t.T)) : kEBins + 1;
+                held = cls > s_sel.cls && cls <= kEBins;
+                const bool edge = cls == s_sel.cls;
+                const unsigned me = __ballot_sync(0xFFFFFFFFu, edge);
+                if (me) {
+                    int base = 0;
+                    if (lane == __ffs(me) - 1) base = atomicAdd(&p.cnt[cin].ticket, __popc(me));
+                    base = __shfl_sync(0xFFFFFFFFu, base, __ffs(me) - 1);
+                    if (edge) held = base + __popc(me & lanes_below) >= s_sel.quota;
+                }
+            }
+            const unsigned mh = __ballot_sync(0xFFFFFFFFu, held);
+            if (lane == 0 && mh) atomicAdd(&p.total_steps[2], (unsigned long long)__popc(mh));
+        }
+        if (held) {
+            copy_out(t, o);
+        } else if (active) {
             bool alive;
-            model = transport_part(p, t, fx, alive);
+            model = transport_part<G>(p, t, fx, alive);
             if (model == kNoInteraction) {
                 finish_step(p, t, alive, fx, o);
-                apply_effects(p, t.ev, t.step, fx);
+                apply_effects(p, t.ev, t.type, t.step, fx);
             }
         }
         {
-            const unsigned ms = __ballot_sync(0xFFFFFFFFu, active);
+            const unsigned ms = __ballot_sync(0xFFFFFFFFu, active && !held);
             if (lane == 0 && ms) atomicAdd(&p.total_steps[0], (unsigned long long)__popc(ms));
         }
-        emit(p, qo, co, lane, o, t.x, t.ev, t.vol);
+        emit(p, qo, co, lane, o, t.x, t.ev, t.vol, select ? s_eh : nullptr);
         // queue the interacting tracks
         const bool need = model != kNoInteraction;
         const unsigned m = __ballot_sync(0xFFFFFFFFu, need);
@@ -100,15 +143,26 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_transport(Params<R> p, int sid
             }
         }
     }
+    if constexpr (select) {
+        __syncthreads();
+        for (int b = threadIdx.x; b < kEBins; b += BS)
+            if (s_eh[b]) atomicAdd(&p.ehist[(size_t)cout * kEBins + b], s_eh[b]);
+    }
 }
 
-template <typename R, int BS>
+template <typename R, int BS, bool S>
 __global__ void __launch_bounds__(BS, 512 / BS) k_interact(Params<R> p, int side, int cin, int cout)
 {
     __shared__ int s_chunk;
     __shared__ int count[kNumModels];
     __shared__ int offset[kNumModels + 1];
     __shared__ unsigned short perm[BS];
+    __shared__ unsigned s_eh[S ? kEBins : 1];
+    constexpr bool select = S;
+    if constexpr (select) {
+        for (int b = threadIdx.x; b < kEBins; b += BS) s_eh[b] = 0u;
+        __syncthreads();
+    }
     const Tracks<R> qi = p.q[side];
     const Tracks<R> qo = p.q[side ^ 1];
     const long long Q = p.Q;
@@ -176,7 +230,7 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_interact(Params<R> p, int side
             fx.dep = iq.dep[r];
             fx.esc = 0.0;
             fx.kill = 0.0;
-            fx.vol = t.vol;
+            fx.col = score_col(p, t.vol, t.x[2]);
             fx.finished = false;
             fx.live_delta = 0;
             interaction_part(p, t, (int)(tv >> 24), fx, o);
@@ -204,7 +258,7 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_interact(Params<R> p, int side
                 }
             }
         }
-        if (stepped) apply_effects(p, t.ev, t.step, fx);
+        if (stepped) apply_effects(p, t.ev, t.type, t.step, fx);
         {
             const unsigned md = __ballot_sync(0xFFFFFFFFu, mine && !stepped);
             if (lane == 0 && md) {
@@ -212,8 +266,12 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_interact(Params<R> p, int side
                 atomicAdd(&p.total_steps[1], (unsigned long long)__popc(md));
             }
         }
-        emit(p, qo, co, lane, o, t.x, t.ev, t.vol);
+        emit(p, qo, co, lane, o, t.x, t.ev, t.vol, select ? s_eh : nullptr);
         __syncthreads();
+    }
+    if constexpr (select) {
+        for (int b = threadIdx.x; b < kEBins; b += BS)
+            if (s_eh[b]) atomicAdd(&p.ehist[(size_t)cout * kEBins + b], s_eh[b]);
     }
 }
 

@@ -60,13 +60,14 @@ struct StepOut {
 
 // Side effects of one step, staged in registers and applied only once the
 // step is committed (a step whose outputs do not fit is discarded and the
-// track is copied unchanged).  Every deposit of a step lands in the volume
-// the track was in before any boundary crossing.
+// track is copied unchanged).  Every deposit of a step is made at the
+// post-step point, in the volume the track was in before any boundary
+// crossing: one histogram column per step.
 struct Effects {
     double dep;   // deposited energy
     double esc;   // escaped energy
     double kill;  // energy of a track killed at the step limit
-    int vol;      // volume of the deposits
+    int col;      // histogram column of the deposits
     bool finished;
     int live_delta;
 };
@@ -85,24 +86,25 @@ enum Model : int {
 };
 
 template <typename R>
-__device__ __forceinline__ void deposit_now(const Params<R>& p, uint32_t ev, int vol, double e)
+__device__ __forceinline__ void deposit_now(const Params<R>& p, uint32_t ev, int col, double e)
 {
     if (e == 0.0) return;
-    int col = p.n_bins;
-    if (vol >= 0) {
-        int b = p.lbin[vol];
-        if (b >= 0 && b < p.n_bins) col = b;
-    }
     atomicAdd(&p.hist[(size_t)ev * p.hstride + col], e);
 }
 
 __device__ __forceinline__ double rest_energy(int type) { return type == 2 ? 2.0 * kMe : 0.0; }
 
+// a track ended after `steps` steps: per-event counts, and the
+// steps-per-track histogram by particle type when it is enabled
 template <typename R>
-__device__ __forceinline__ void finish_track(const Params<R>& p, uint32_t ev, uint32_t steps)
+__device__ __forceinline__ void finish_track(const Params<R>& p, uint32_t ev, int type, uint32_t steps)
 {
     atomicAdd(&p.counts[2 * (size_t)ev + 0], (unsigned long long)steps);
     atomicAdd(&p.counts[2 * (size_t)ev + 1], 1ull);
+    if (p.step_hist) {
+        const uint32_t last = (uint32_t)(p.step_bins - 1);
+        atomicAdd(&p.step_hist[(size_t)type * p.step_bins + (steps < last ? steps : last)], 1ull);
+    }
 }
 
 // An event is finished when its live-track count reaches zero.  A thread
@@ -120,12 +122,13 @@ __device__ __forceinline__ void update_live(const Params<R>& p, uint32_t ev, int
 }
 
 template <typename R>
-__device__ __forceinline__ void apply_effects(const Params<R>& p, uint32_t ev, uint32_t steps, const Effects& fx)
+__device__ __forceinline__ void apply_effects(const Params<R>& p, uint32_t ev, int type, uint32_t steps,
+                                              const Effects& fx)
 {
-    deposit_now(p, ev, fx.vol, fx.dep);
+    deposit_now(p, ev, fx.col, fx.dep);
     if (fx.esc != 0.0) atomicAdd(&p.ledger[3 * (size_t)ev + 0], fx.esc);
     if (fx.kill != 0.0) atomicAdd(&p.ledger[3 * (size_t)ev + 1], fx.kill);
-    if (fx.finished) finish_track(p, ev, steps);
+    if (fx.finished) finish_track(p, ev, type, steps);
     update_live(p, ev, fx.live_delta);
 }
 
@@ -141,13 +144,12 @@ __device__ __forceinline__ void apply_effects(const Params<R>& p, uint32_t ev, u
 //    a null interaction.
 // Returns the model to sample in phase B, or kNoInteraction.  `alive`
 // reports whether the track survives phase A.
-template <typename R>
+template <int G, typename R>
 __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t, Effects& fx, bool& alive)
 {
     fx.dep = 0.0;
     fx.esc = 0.0;
     fx.kill = 0.0;
-    fx.vol = t.vol;
     fx.finished = false;
     fx.live_delta = 0;
     const uint64_t event_id = p.event_id[t.ev];
@@ -204,16 +206,43 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
     const double s_physd = to_d(s_phys);
     if (!(charged && p.has_field)) {
         const double ud[3] = {to_d(t.u[0]), to_d(t.u[1]), to_d(t.u[2])};
-        e = nav_exit(p, t.vol, t.x, ud);
-        if (e.t <= s_physd) {
-            s = e.t;
-            boundary = true;
-        } else {
-            s = s_physd;
-        }
+        if constexpr (G == kGeomCylinders) {
+            // cylinders (thick shells, navigation with square roots): a
+            // physics step that ends more than the chord margin inside the
+            // shell has an exit distance above s_phys by at least the
+            // margin (far above its rounding): no boundary, exactly as the
+            // full navigation would decide
+            double x1[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) t.x[a] = t.x[a] + s * ud[a];
-        if (boundary && e.axis >= 0) t.x[e.axis] = e.plane;
+            for (int a = 0; a < 3; ++a) x1[a] = t.x[a] + s_physd * ud[a];
+            if (!chord_inside<G>(p, t.vol, t.x, x1)) {
+                e = nav_exit<G>(p, t.vol, t.x, ud);
+                boundary = e.t <= s_physd;
+            }
+            if (boundary) {
+                s = e.t;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) t.x[a] = t.x[a] + s * ud[a];
+                if (e.axis >= 0) t.x[e.axis] = e.plane;
+            } else {
+                s = s_physd;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) t.x[a] = x1[a];
+            }
+        } else {
+            // thin layers: most steps cross a plane; the navigation (with
+            // its FP32 prefilter) is cheaper than a test that mostly fails
+            e = nav_exit<G>(p, t.vol, t.x, ud);
+            if (e.t <= s_physd) {
+                s = e.t;
+                boundary = true;
+            } else {
+                s = s_physd;
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) t.x[a] = t.x[a] + s * ud[a];
+            if (boundary && e.axis >= 0) t.x[e.axis] = e.plane;
+        }
     } else {
         double smax = s_physd;
         if (smax > p.max_field_step) {
@@ -230,10 +259,11 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
             interact = false;
         }
         bool crossed = false;
-        s = propagate_field(p, t.type == 1 ? -1 : 1, Td, t.vol, t.x, t.u, smax, &e, &crossed);
+        s = propagate_field<G>(p, t.type == 1 ? -1 : 1, Td, t.vol, t.x, t.u, smax, &e, &crossed);
         boundary = crossed;
     }
     if (boundary) interact = false;
+    fx.col = score_col(p, t.vol, t.x[2]);
 
     alive = true;
     // 6-7: continuous loss
@@ -428,10 +458,13 @@ __device__ __forceinline__ void copy_out(const TrackReg<R>& t, StepOut<R>& o)
 }
 
 // warp-aggregated reservation and store of each lane's outputs (all lanes
-// of the warp call it); counts are packed as photons | charged << 16
+// of the warp call it); counts are packed as photons | charged << 16.
+// With track selection on, eh (shared memory) counts the outputs' energy
+// classes.
 template <typename R>
 __device__ __forceinline__ void emit(const Params<R>& p, const Tracks<R>& qo, Counters* cout, int lane,
-                                     const StepOut<R>& o, const double x[3], uint32_t ev, int vol)
+                                     const StepOut<R>& o, const double x[3], uint32_t ev, int vol,
+                                     unsigned* eh = nullptr)
 {
     int ng = 0, nc = 0;
     for (int k = 0; k < o.n; ++k) {
@@ -474,7 +507,58 @@ __device__ __forceinline__ void emit(const Params<R>& p, const Tracks<R>& qo, Co
             continue;
         }
         store_track(qo, dst, x, o.u[k], o.T[k], o.uid[k], ev, o.step[k], o.type[k], vol);
+        if (eh) atomicAdd(&eh[energy_class(est_f(o.T[k]))], 1u);
     }
+}
+
+// Track selection (the paper's Sec. 4: preferring low-energy tracks keeps
+// the number of tracks in flight, and so the capacity needed, down).  The
+// lowest-energy class c* whose cumulative count over the input reaches
+// max_active, and the quota of tracks of class c* that may still step.
+// One warp computes it from the input slot's energy-class counts.
+struct Selection {
+    int cls;    // classes below step, above are held; kEBins: all step
+    int quota;  // tickets of class cls that step
+};
+
+template <typename R>
+__device__ __forceinline__ Selection select_threshold(const Params<R>& p, int cin, int lane)
+{
+    const unsigned* h = p.ehist + (size_t)cin * kEBins;
+    unsigned c[kEBins / 32];
+    long long local = 0;
+#pragma unroll
+    for (int k = 0; k < kEBins / 32; ++k) {
+        c[k] = h[lane * (kEBins / 32) + k];
+        local += c[k];
+    }
+    long long incl = local;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const long long y = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    const long long A = p.max_active;
+    const unsigned reach = __ballot_sync(0xFFFFFFFFu, incl >= A);
+    Selection sel;
+    sel.cls = kEBins;
+    sel.quota = 0;
+    if (!reach) return sel;
+    const int L = __ffs(reach) - 1;
+    if (lane == L) {
+        long long cum = incl - local;
+#pragma unroll
+        for (int k = 0; k < kEBins / 32; ++k) {
+            if (sel.cls == kEBins && cum + c[k] >= A) {
+                sel.cls = lane * (kEBins / 32) + k;
+                sel.quota = (int)(A - cum);
+            }
+            cum += c[k];
+        }
+    }
+    sel.cls = __shfl_sync(0xFFFFFFFFu, sel.cls, L);
+    sel.quota = __shfl_sync(0xFFFFFFFFu, sel.quota, L);
+    return sel;
 }
 
 // shared-memory records of the tracks that interact in one chunk, sorted by
@@ -508,7 +592,7 @@ struct Staging {
 // is copied unchanged (its step counter, hence its random stream, is kept).
 // Only interactions make two outputs.  When 2n <= Q every step fits and no
 // token is counted.
-template <typename R, int BS>
+template <typename R, int BS, int G>
 __global__ void __launch_bounds__(BS, 512 / BS) k_step(Params<R> p, int side, int cin, int cout, int cclr)
 {
     __shared__ int s_chunk;
@@ -554,10 +638,10 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_step(Params<R> p, int side, in
         if (active) {
             load_track(qi, src, t);
             bool alive;
-            model = transport_part(p, t, fx, alive);
+            model = transport_part<G>(p, t, fx, alive);
             if (model == kNoInteraction) {
                 finish_step(p, t, alive, fx, o);
-                apply_effects(p, t.ev, t.step, fx);
+                apply_effects(p, t.ev, t.type, t.step, fx);
             } else {
                 rank = atomicAdd(&sg.count[model], 1);
             }
@@ -619,7 +703,7 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_step(Params<R> p, int side, in
             fx.dep = sg.dep[tid];
             fx.esc = 0.0;
             fx.kill = 0.0;
-            fx.vol = t.vol;
+            fx.col = score_col(p, t.vol, t.x[2]);
             fx.finished = false;
             fx.live_delta = 0;
             interaction_part(p, t, (int)sg.model[tid], fx, o);
@@ -647,7 +731,7 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_step(Params<R> p, int side, in
                 }
             }
         }
-        if (stepped) apply_effects(p, t.ev, t.step, fx);
+        if (stepped) apply_effects(p, t.ev, t.type, t.step, fx);
         {
             const unsigned md = __ballot_sync(0xFFFFFFFFu, mine && !stepped);
             if (lane == 0 && md) {
@@ -684,17 +768,7 @@ __global__ void k_admit(Params<R> p, int side, int cs, int n, const int32_t* ev,
         t.u[2] = R(dir[3 * i + 2]);
         t.uid = uid_of[i];
         t.step = 0;
-        // locate: inside the stack box -> layer; inside the world -> world
-        int vol;
-        if (t.x[0] >= -p.hx && t.x[0] <= p.hx && t.x[1] >= -p.hy && t.x[1] <= p.hy && t.x[2] >= p.zb[0] &&
-            t.x[2] <= p.zb[p.n_layers]) {
-            vol = layer_at(p.zb, p.n_layers, t.x[2]);
-        } else if (t.x[0] < p.wlo[0] || t.x[0] > p.whi[0] || t.x[1] < p.wlo[1] || t.x[1] > p.whi[1] ||
-                   t.x[2] < p.wlo[2] || t.x[2] > p.whi[2]) {
-            vol = kVolOut;
-        } else {
-            vol = kVolWorld;
-        }
+        const int vol = locate_volume(p, t.x);
         t.vol = vol;
         double E = (double)T[i] + rest_energy(t.type);
         if (t.type < 0 || t.type > 2) {
@@ -704,10 +778,11 @@ __global__ void k_admit(Params<R> p, int side, int cs, int n, const int32_t* ev,
             if (vol == kVolOut) {
                 atomicAdd(&p.ledger[3 * (size_t)t.ev + 0], E);
             } else if (T[i] < p.cut[t.type]) {
-                deposit_now(p, t.ev, vol, E);
+                deposit_now(p, t.ev, score_col(p, vol, t.x[2]), E);
             } else {
                 keep = true;
                 atomicAdd(&p.live[t.ev], 1);
+                if (p.max_active > 0) atomicAdd(&p.ehist[(size_t)cs * kEBins + energy_class(est_f(t.T))], 1u);
             }
         }
     }
@@ -753,6 +828,7 @@ __global__ void k_set_tracks(Params<R> p, int side, int cs, int n, const double*
         return;
     }
     atomicAdd(&p.live[slot[i]], 1);
+    if (p.max_active > 0) atomicAdd(&p.ehist[(size_t)cs * kEBins + energy_class(est_f(R(r[1])))], 1u);
     store_track(p.q[side], dst, x, u, R(r[1]), uid[i], (uint32_t)slot[i], (uint32_t)r[9], type, (int)r[8]);
 }
 

@@ -18,6 +18,7 @@ HOST, DEVICE = 0, 1
 PRECISION = {"fp64": 0, "mixed": 1}
 LOOP = {"plain": 0, "graph": 1}
 SCHEDULE = {"fused": 0, "split": 1}
+SELECT = {"order": 0, "low_energy": 1}
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "CAPACITY", -3: "CUDA", -4: "BAD_STATE", -5: "TIMEOUT",
           -6: "NOT_READY", -7: "HOST_OOM"}
 SUMMARY_FIELDS = ("edep", "escaped", "killed", "e_in", "n_steps", "n_tracks")
@@ -34,7 +35,9 @@ class Options(ctypes.Structure):
                 ("max_events", ctypes.c_int32), ("max_bins", ctypes.c_int32), ("block_size", ctypes.c_int32),
                 ("loop_mode", ctypes.c_int32), ("graph_steps", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("seed", ctypes.c_uint32),
-                ("cuda_stream", ctypes.c_void_p), ("device_pool", ctypes.c_void_p), ("pool_bytes", ctypes.c_size_t)]
+                ("cuda_stream", ctypes.c_void_p), ("device_pool", ctypes.c_void_p), ("pool_bytes", ctypes.c_size_t),
+                ("step_hist_bins", ctypes.c_int32), ("select_policy", ctypes.c_int32),
+                ("max_active", ctypes.c_int64)]
 
 
 class Material(ctypes.Structure):
@@ -56,7 +59,9 @@ class World(ctypes.Structure):
     _fields_ = [("z0_cm", ctypes.c_double), ("half_x_cm", ctypes.c_double), ("half_y_cm", ctypes.c_double),
                 ("lo_cm", ctypes.c_double * 3), ("hi_cm", ctypes.c_double * 3), ("B_tesla", ctypes.c_double * 3),
                 ("rk_delta_cm", ctypes.c_double), ("max_field_step_cm", ctypes.c_double),
-                ("max_steps", ctypes.c_int32), ("n_bins", ctypes.c_int32)]
+                ("max_steps", ctypes.c_int32), ("n_bins", ctypes.c_int32), ("geometry", ctypes.c_int32),
+                ("score_z", ctypes.c_int32), ("half_z_cm", ctypes.c_double), ("score_z_lo_cm", ctypes.c_double),
+                ("score_z_hi_cm", ctypes.c_double)]
 
 
 class Primaries(ctypes.Structure):
@@ -72,10 +77,15 @@ class ServeOptions(ctypes.Structure):
 SERVE = {"continuous": 0, "batch": 1}
 
 
+class StepRecord(ctypes.Structure):
+    _fields_ = [("photons", ctypes.c_int64), ("charged", ctypes.c_int64), ("interacting", ctypes.c_int64),
+                ("deferred", ctypes.c_int64), ("held", ctypes.c_int64), ("ms", ctypes.c_double)]
+
+
 class RunStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int64), ("track_steps", ctypes.c_int64), ("peak_tracks", ctypes.c_int64),
                 ("deferred", ctypes.c_int64), ("live_tracks", ctypes.c_int64), ("state_bytes", ctypes.c_int64),
-                ("kernel_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int32)]
+                ("kernel_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int32), ("held", ctypes.c_int64)]
 
 
 _lib = None
@@ -94,6 +104,9 @@ _SIGS = {
     "emt_submit": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(Primaries),
                                     ctypes.c_int32]),
     "emt_run": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(RunStats)]),
+    "emt_run_traced": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(RunStats),
+                                        ctypes.POINTER(StepRecord), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "emt_read_step_hist": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]),
     "emt_poll": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "emt_read_event": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
     "emt_read_all": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -176,6 +189,11 @@ def world_struct(world) -> World:
     s.max_steps = int(w[13])
     s.n_bins = int(w[14])
     s.max_field_step_cm = w[15]
+    if len(w) >= 21:
+        s.geometry = int(w[16])
+        s.half_z_cm = w[17]
+        s.score_z = int(w[18])
+        s.score_z_lo_cm, s.score_z_hi_cm = w[19], w[20]
     return s
 
 
@@ -184,7 +202,8 @@ class Context:
 
     def __init__(self, *, device: int = 0, precision: str = "fp64", slot_capacity: int = 1 << 22,
                  max_events: int = 10000, max_bins: int = 128, block_size: int = 0, loop_mode: str = "plain",
-                 graph_steps: int = 12, seed: int = 1, use_torch_pool: bool = True, schedule: str = "fused"):
+                 graph_steps: int = 12, seed: int = 1, use_torch_pool: bool = True, schedule: str = "fused",
+                 step_hist_bins: int = 0, max_active: int = 0, select: str = "order"):
         import torch
         L = lib()
         self._torch = torch
@@ -200,6 +219,9 @@ class Context:
         o.graph_steps = int(graph_steps)
         o.schedule = SCHEDULE[schedule]
         o.seed = int(seed) & 0xFFFFFFFF
+        o.step_hist_bins = int(step_hist_bins)
+        o.max_active = int(max_active)
+        o.select_policy = SELECT[select]
         self.device = torch.device("cuda", device)
         self.stream = torch.cuda.Stream(device=self.device)
         o.cuda_stream = ctypes.c_void_p(self.stream.cuda_stream)
@@ -294,6 +316,24 @@ class Context:
         st = RunStats()
         self._check(lib().emt_run(self._h, int(max_iterations), ctypes.byref(st)))
         return {f: getattr(st, f) for f, _ in RunStats._fields_}
+
+    def run_traced(self, max_iterations: int = 0, cap: int = 1 << 16):
+        """emt_run_traced: (stats, records[n, 6] = photons, charged,
+        interacting, deferred, held, ms per iteration)."""
+        st = RunStats()
+        rec = (StepRecord * cap)()
+        n = ctypes.c_int32()
+        self._check(lib().emt_run_traced(self._h, int(max_iterations), ctypes.byref(st), rec, cap, ctypes.byref(n)))
+        out = np.array([[r.photons, r.charged, r.interacting, r.deferred, r.held, r.ms] for r in rec[: n.value]],
+                       np.float64).reshape(-1, 6)
+        return {f: getattr(st, f) for f, _ in RunStats._fields_}, out
+
+    def read_step_hist(self, reset: bool = False) -> np.ndarray:
+        """Steps-per-track histogram [3, step_hist_bins] (gamma, e-, e+)."""
+        nb = int(self.options.step_hist_bins)
+        out = np.zeros((3, max(nb, 1)), np.uint64)
+        self._check(lib().emt_read_step_hist(self._h, _ptr(out), nb, int(bool(reset))))
+        return out
 
     def poll(self, cap: int = 65536):
         out = np.zeros(cap, np.uint64)

@@ -118,7 +118,7 @@ def test_straight_photons_count_surfaces(oracle_mod):
 
 def test_z_scoring_bins(oracle_mod):
     """Primaries below the cut deposit at their starting point: the energy
-    lands in bin floor((z + H) / (2H / n_bins))."""
+    lands in bin floor((z + H) * n_bins / 2H)."""
     s = W.cms_setup()
     o = make(oracle_mod, s)
     zs = [-H + 1.0, -5.0, 0.0, 5.0, 4.999, 699.9, 123.4]
@@ -127,9 +127,9 @@ def test_z_scoring_bins(oracle_mod):
             "T": np.full(n, 0.5), "pos": np.array([[50.0, 0.0, z] for z in zs]),
             "dir": np.tile([0.0, 0.0, 1.0], (n, 1))}
     hist, summ = o.run(prim, n, np.arange(n))
-    w = 2 * H / s.n_bins
+    scale = s.n_bins / (2 * H)
     for i, z in enumerate(zs):
-        b = int(np.floor((z + H) / w))
+        b = int(np.floor((z + H) * scale))
         assert hist[i, b] == 0.5 and hist[i].sum() == 0.5
 
 
