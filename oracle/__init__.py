@@ -24,9 +24,11 @@ _LIB = os.path.join(_HERE, "libemt_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-# process ids of orc_sample
-PHOTO, COMPTON, PAIR, IONI, BREMS, ANNIH, BHABHA = range(7)
+# process ids of orc_sample (7, 8: with the angular option)
+PHOTO, COMPTON, PAIR, IONI, BREMS, ANNIH, BHABHA, BREMS_ANGULAR, PAIR_ANGULAR = range(9)
 ALL_PROCESSES = 63
+MSC = 64        # process-mask bit: multiple scattering of e+-
+ANGULAR = 128   # process-mask bit: angular distributions of brems and pair
 
 
 def build(force: bool = False) -> str:
@@ -71,6 +73,8 @@ def lib():
                 "orc_dedx_coll": (d, [d, d, d, d, i32, d, d]),
                 "orc_gauss_legendre": (None, [i32, p, p]),
                 "orc_sample": (i32, [i32, d, d, d, u32, u64, u64, u32, p]),
+                "orc_highland": (d, [d, d, d]),
+                "orc_msc": (i32, [d, d, d, u32, u64, u64, u32, p]),
                 "orc_create": (p, [p, i32, p, p, i32, p, u32]),
                 "orc_destroy": (None, [p]),
                 "orc_grid_size": (i32, [p]),
@@ -127,6 +131,17 @@ def sample(process: int, E: float, cut_e: float, cut_g: float, seed: int, event_
     out = np.zeros(16)
     lib().orc_sample(process, E, cut_e, cut_g, seed, event_id, uid, step, _ptr(out))
     return out
+
+
+def highland(T, s, x0_cm) -> float:
+    return lib().orc_highland(T, s, x0_cm)
+
+
+def msc(T, s, x0_cm, direction, seed, event_id, uid, step=0) -> np.ndarray:
+    """Direction after multiple scattering over a step of length s."""
+    d = np.ascontiguousarray(direction, np.float64).copy()
+    lib().orc_msc(T, s, x0_cm, seed, event_id, uid, step, _ptr(d))
+    return d
 
 
 # ---------------------------------------------------------------- setup

@@ -970,7 +970,31 @@ static void sample_compton(draws_t* d, double k, double dir[3], products_t* out,
 
 /* Bethe-Heitler (complete screening): x uniform on [eps0, 1-eps0],
  * accept with 1 - 4/3 x(1-x) (<= 1).  Both leptons along the photon. */
-static void sample_pair(draws_t* d, double k, const double dir[3], products_t* out)
+/* Angular distribution of a lepton or photon emitted by a lepton of
+ * kinetic energy T (angular option, process bit ORC_ANGULAR): the dipole
+ * form dN/dcos(theta) ~ (1 - beta cos(theta))^-2, whose width is ~1/gamma
+ * (the leading behaviour of the Sauter and Schiff distributions).
+ * Inverting its cumulative distribution at u gives, with a = 1 - beta,
+ * 1 - cos(theta) = 2 a (1 - u) / (a + 2 beta u), free of cancellation as
+ * beta -> 1 (a = me^2 / (E (E + p)) computed directly). */
+static double dipole_one_minus_cos(double T, double u)
+{
+    double E = T + ME;
+    double p = sqrt(T * (T + 2.0 * ME));
+    double beta = p / E;
+    double a = ME * ME / (E * (E + p));
+    return 2.0 * a * (1.0 - u) / (a + 2.0 * beta * u);
+}
+
+/* direction at polar angle theta (1 - cos given) and azimuth phi about dir */
+static void emit_dir(const double dir[3], double omc, double phi, double out[3])
+{
+    double cost = 1.0 - omc;
+    if (cost < -1.0) cost = -1.0;
+    rotate(dir, cost, phi, out);
+}
+
+static void sample_pair(draws_t* d, double k, const double dir[3], products_t* out, int angular)
 {
     double eps0 = ME / k;
     double w = 1.0 - 2.0 * eps0;
@@ -990,9 +1014,16 @@ static void sample_pair(draws_t* d, double k, const double dir[3], products_t* o
     out->T[0] = Tm;
     out->type[1] = 2;
     out->T[1] = Tp;
-    for (int a = 0; a < 3; ++a) {
-        out->dir[0][a] = dir[a];
-        out->dir[1][a] = dir[a];
+    if (angular) {
+        /* each lepton at its own dipole angle; azimuths phi and phi + pi */
+        double um = draw(d), phi = 2.0 * PI * draw(d), up = draw(d);
+        emit_dir(dir, dipole_one_minus_cos(Tm, um), phi, out->dir[0]);
+        emit_dir(dir, dipole_one_minus_cos(Tp, up), phi + PI, out->dir[1]);
+    } else {
+        for (int a = 0; a < 3; ++a) {
+            out->dir[0][a] = dir[a];
+            out->dir[1][a] = dir[a];
+        }
     }
     out->parent_alive = 0;
 }
@@ -1011,7 +1042,8 @@ static void sample_photo(double k, double bk, const double dir[3], products_t* o
 
 /* bremsstrahlung: k = kc (T/kc)^u (1/k envelope), accept with
  * (4/3 - 4/3 y + y^2)/(4/3); photon along the lepton */
-static void sample_brems(draws_t* d, double T, double kc, const double dir[3], products_t* out, double* Tnew)
+static void sample_brems(draws_t* d, double T, double kc, const double dir[3], products_t* out, double* Tnew,
+                         int angular)
 {
     double E = T + ME;
     double lr = log(T / kc);
@@ -1026,7 +1058,14 @@ static void sample_brems(draws_t* d, double T, double kc, const double dir[3], p
     out->n = 1;
     out->type[0] = 0;
     out->T[0] = k;
-    for (int a = 0; a < 3; ++a) out->dir[0][a] = dir[a];
+    if (angular) {
+        /* photon at the dipole angle of the radiating lepton; the lepton
+         * keeps its direction (the nucleus takes the recoil) */
+        double u = draw(d), phi = 2.0 * PI * draw(d);
+        emit_dir(dir, dipole_one_minus_cos(T, u), phi, out->dir[0]);
+    } else {
+        for (int a = 0; a < 3; ++a) out->dir[0][a] = dir[a];
+    }
     *Tnew = T - k;
     out->parent_alive = 1;
 }
@@ -1147,9 +1186,11 @@ int orc_sample(int process, double E, double cut_e, double cut_g, uint32_t seed,
     switch (process) {
     case P_PHOTO: sample_photo(E, cut_e, dir, &pr); Enew = 0.0; break;
     case P_COMPTON: sample_compton(&dr, E, dir, &pr, &Enew); break;
-    case P_PAIR: sample_pair(&dr, E, dir, &pr); Enew = 0.0; break;
+    case P_PAIR: sample_pair(&dr, E, dir, &pr, 0); Enew = 0.0; break;
+    case 8: sample_pair(&dr, E, dir, &pr, 1); Enew = 0.0; break;
     case P_IONI: sample_moller(&dr, E, cut_e, dir, &pr, &Enew); break;
-    case P_BREMS: sample_brems(&dr, E, cut_g, dir, &pr, &Enew); break;
+    case P_BREMS: sample_brems(&dr, E, cut_g, dir, &pr, &Enew, 0); break;
+    case 7: sample_brems(&dr, E, cut_g, dir, &pr, &Enew, 1); break;
     case P_ANNIH: sample_annih(&dr, E, dir, &pr); Enew = 0.0; break;
     case 6: sample_bhabha(&dr, E, cut_e, dir, &pr, &Enew); break;
     default: return -1;
@@ -1298,9 +1339,56 @@ static void deposit(const orc_handle* h, tally_t* t, int vol, double z, double e
 
 static double rest_energy(int type) { return type == 2 ? 2.0 * ME : 0.0; }
 
+/* ------------------------------------------------------------------ */
+/* Multiple scattering of e+- (process bit ORC_MSC; Table 1 lists Urban */
+/* and WentzelVI, whose data and tuned parameters are not available).  */
+/* A reading with a published closed form: after a step of length s in */
+/* matter the direction turns by a polar angle whose two projections   */
+/* are independent Gaussians of width theta0 from Highland's formula    */
+/* (PDG review "Passage of particles through matter", Eq. 34.15, unit  */
+/* charge): theta0 = 13.6 MeV / (beta p) sqrt(s/X0) [1 + 0.038         */
+/* ln(s / (X0 beta^2))], with the pre-step momentum, clamped at 0 where */
+/* the bracket turns negative (s/X0 < 1e-11).  The space angle is then */
+/* theta = theta0 sqrt(-2 ln u_a), the azimuth 2 pi u_b (u_a, u_b: the  */
+/* step's draws MSC_DRAW, MSC_DRAW + 1), capped at pi.  No lateral     */
+/* displacement and no path-length correction.                         */
+/* ------------------------------------------------------------------ */
+#define MSC_DRAW (1u << 20)
+
+double orc_highland(double T, double s, double x0_cm)
+{
+    double p = sqrt(T * (T + 2.0 * ME));
+    double beta = p / (T + ME);
+    double t = s / x0_cm;
+    double f = 1.0 + 0.038 * log(t / (beta * beta));
+    if (!(f > 0.0)) return 0.0;
+    return 13.6 / (beta * p) * sqrt(t) * f;
+}
+
+static void msc_deflect(draws_t* d, double T, double s, double x0_cm, double u[3])
+{
+    double th0 = orc_highland(T, s, x0_cm);
+    if (!(th0 > 0.0)) return;
+    d->next = MSC_DRAW;
+    double ua = draw(d), ub = draw(d);
+    double th = th0 * sqrt(-2.0 * log(ua));
+    if (th > PI) th = PI;
+    double out[3];
+    rotate(u, cos(th), 2.0 * PI * ub, out);
+    memcpy(u, out, sizeof out);
+}
+
+int orc_msc(double T, double s, double x0_cm, uint32_t seed, uint64_t event_id, uint64_t uid, uint32_t step,
+            double* dir)
+{
+    draws_t dr = {seed, event_id, uid, step, 0};
+    msc_deflect(&dr, T, s, x0_cm, dir);
+    return (int)dr.next;
+}
+
 typedef struct {
     double s, edep;
-    int boundary, interacted, process, alive;
+    int boundary, interacted, process, alive, msc;
     int n_sec;
     track_t sec[2];
 } step_result_t;
@@ -1392,7 +1480,8 @@ static void step_track(const orc_handle* h, uint64_t event_id, track_t* tr, tall
     res->s = s;
     res->boundary = boundary;
     int alive = 1;
-    /* 6-7: continuous loss */
+    /* 6-7: continuous loss (and 6b: multiple scattering) */
+    const double T0 = tr->T;
     if (charged && m) {
         double r = R - s;
         double Tn = r > 0.0 ? inv_range_of(h, tab(h, mi, tr->type, 3), r) : 0.0;
@@ -1406,6 +1495,12 @@ static void step_track(const orc_handle* h, uint64_t event_id, track_t* tr, tall
             res->edep += e2;
             alive = 0;
         }
+    }
+    /* 6b: multiple scattering at the post-step point of a charged step in
+     * matter (boundary steps included) */
+    if (alive && charged && m && (h->mask & ORC_MSC) && s > 0.0) {
+        msc_deflect(&dr, T0, s, m->x0_cm, tr->u);
+        res->msc = 1;
     }
     /* 8: boundary */
     if (alive && boundary) {
@@ -1450,7 +1545,7 @@ static void step_track(const orc_handle* h, uint64_t event_id, track_t* tr, tall
         case P_COMPTON: sample_compton(&dr, T, tr->u, &pr, &tr->T); break;
         case P_PAIR:
             if (T > 2.0 * ME)
-                sample_pair(&dr, T, tr->u, &pr);
+                sample_pair(&dr, T, tr->u, &pr, (h->mask & ORC_ANGULAR) != 0);
             else
                 pr.null_interaction = 1;
             break;
@@ -1469,7 +1564,7 @@ static void step_track(const orc_handle* h, uint64_t event_id, track_t* tr, tall
             break;
         case P_BREMS:
             if (T > kc)
-                sample_brems(&dr, T, kc, tr->u, &pr, &tr->T);
+                sample_brems(&dr, T, kc, tr->u, &pr, &tr->T, (h->mask & ORC_ANGULAR) != 0);
             else
                 pr.null_interaction = 1;
             break;

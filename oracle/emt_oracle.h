@@ -30,6 +30,8 @@ extern "C" {
 #define ORC_IONI 8u
 #define ORC_BREMS 16u
 #define ORC_ANNIH 32u
+#define ORC_MSC 64u     /* multiple scattering of e+- (Highland width) */
+#define ORC_ANGULAR 128u /* dipole angular distributions for brems and pair */
 
 typedef struct orc_handle orc_handle;
 
@@ -63,9 +65,15 @@ double orc_dedx_coll(double Z, double A, double rho, double I_eV, int charge,
 void orc_gauss_legendre(int n, double* x, double* w);
 
 /* ---- samplers (single interaction, from a track's draw stream) ---- */
-/* out layout per sampler documented in emt_oracle.c */
+/* out layout per sampler documented in emt_oracle.c; process 7 and 8 are
+ * bremsstrahlung and pair production with the angular option */
 int orc_sample(int process, double E, double cut_e, double cut_g, uint32_t seed,
                uint64_t event_id, uint64_t uid, uint32_t step, double* out);
+/* multiple scattering: Highland width, and the deflection of dir (in
+ * place) after a step of length s at pre-step kinetic energy T */
+double orc_highland(double T, double s, double x0_cm);
+int orc_msc(double T, double s, double x0_cm, uint32_t seed, uint64_t event_id,
+            uint64_t uid, uint32_t step, double* dir);
 
 /* ---- set-up ---- */
 /* materials: n x {Z, A, rho, I_eV, bk_MeV}; rho == 0 -> vacuum
