@@ -39,6 +39,28 @@ from paper_2203_09467_gb300 import workloads as W  # noqa: E402
 
 METRIC = "track-steps/s"
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the step
+# kernels per track-step, from one ncu capture of every k_transport and
+# k_interact launch of a smaller run of the same workload (the summary and
+# the command are in profiles/).  It is reported only while the kernel
+# sources are the ones that were measured (their SHA-256 below).
+TRAFFIC = {
+    "kernel_sha256": "c54e181b34f9681d0fdf7fb6b0920b31255839c339262ed1b18849fbae1e02c7",
+    "bytes_per_track_step": {"calo/fp64": 101.88, "calo/mixed": 79.23},
+    "source": "profiles/step_kernels_calo_dram_traffic.md",
+}
+KERNEL_SOURCES = ["emt_device.cuh", "emt_step.cuh", "emt_split.cuh", "emt_launch.cuh", "emt_kernels_fp64.cu",
+                  "emt_kernels_mixed.cu"]
+
+
+def kernel_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2203_09467_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
 
 def load_peaks():
     try:
@@ -315,23 +337,32 @@ def gpu_arm(args):
             "launches": kern_launch, "mean_launch_ms": kern_ms / max(kern_launch, 1),
             "algorithmic_bytes_per_launch": state_bytes / max(kern_launch, 1),
             "kernel_share_of_step": kern_ms / total_ms}
+    per_step = TRAFFIC["bytes_per_track_step"].get(f"{args.workload}/{args.precision}")
     if args.traffic_per_launch:
         roof["traffic"] = args.traffic_per_launch
+    elif per_step and TRAFFIC["kernel_sha256"] == kernel_sha256():
+        roof["traffic"] = per_step * steps_done / max(kern_launch, 1)
+        roof["traffic_source"] = (f"{TRAFFIC['source']}: {per_step:.1f} B per track-step x "
+                                  f"{steps_done / max(kern_launch, 1):.0f} track-steps per launch")
 
     # the plain form: the same events submitted and run one at a time
     forms = None
     if args.one_at_a_time > 0 and rank == 0:
         k = min(args.one_at_a_time, n)
         single = emt.context_for(setup, device=local, precision=args.precision, slot_capacity=1 << 22,
-                                 max_events=1, block_size=cfg["block_size"], loop_mode="plain")
+                                 max_events=1, block_size=cfg["block_size"], loop_mode="plain",
+                                 schedule=cfg.get("schedule", "split"))
+        # primaries of event e: [first[e], first[e + 1]) (grouped by event)
+        first = np.searchsorted(prim["event"], np.arange(n + 1))
         steps1 = 0
         torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(single.stream)
         for e in range(k):
-            sub = {kk: v[e:e + 1] for kk, v in dprim.items()}
-            sub["event"] = torch.zeros(1, dtype=torch.int32, device=dev)
+            lo, hi = int(first[e]), int(first[e + 1])
+            sub = {kk: v[lo:hi] for kk, v in dprim.items()}
+            sub["event"] = torch.zeros(hi - lo, dtype=torch.int32, device=dev)
             single.submit(ids[e:e + 1], sub)
             steps1 += single.run()["track_steps"]
             single.read_all(hist_d[e:e + 1], summ_d[e:e + 1])
@@ -345,6 +376,8 @@ def gpu_arm(args):
                                    "sample_events": k}}
 
     ctx.close()
+    if args.diagnostics and rank == 0:
+        diagnostics(args, emt, setup, prim, ids, cfg, local)
     if rank != 0:
         if world > 1:
             dist.barrier()
@@ -377,6 +410,28 @@ def gpu_arm(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def diagnostics(args, emt, setup, prim, ids, cfg, device):
+    """Sec. 4's diagnostics of one untimed run of the workload: tracks in
+    flight, interactions, deferred and held copies and device time per step
+    (plain driver), and the steps-per-track histogram by particle type."""
+    nb = 4096
+    ctx = emt.context_for(setup, device=device, precision=args.precision, slot_capacity=args.slots,
+                          max_events=len(ids), block_size=cfg["block_size"], schedule=cfg.get("schedule", "split"),
+                          step_hist_bins=nb)
+    ctx.submit(ids, prim)
+    st, rec = ctx.run_traced()
+    ctx.read_all()
+    sh = ctx.read_step_hist()
+    ctx.close()
+    out = {"workload": args.workload, "precision": args.precision, "stats": st,
+           "records": {"photons": rec[:, 0].tolist(), "charged": rec[:, 1].tolist(),
+                       "interacting": rec[:, 2].tolist(), "deferred": rec[:, 3].tolist(),
+                       "held": rec[:, 4].tolist(), "ms": rec[:, 5].tolist()},
+           "steps_per_track": {"gamma": sh[0].tolist(), "electron": sh[1].tolist(), "positron": sh[2].tolist()}}
+    with open(args.diagnostics, "w") as f:
+        json.dump(out, f)
 
 
 def served_arm(args):
@@ -448,6 +503,8 @@ def main():
     ap.add_argument("--ref-events", type=int, default=1000)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--diagnostics", default=None,
+                    help="write per-step records and the steps-per-track histogram of one untimed run (JSON)")
     ap.add_argument("--traffic-per-launch", type=float, default=None,
                     help="DRAM bytes per step-kernel launch from an ncu capture of this kernel")
     args = ap.parse_args()

@@ -67,7 +67,23 @@ typedef int32_t emt_status;
 #define EMT_IONI 8u
 #define EMT_BREMS 16u
 #define EMT_ANNIH 32u
-#define EMT_ALL_PROCESSES 63u
+#define EMT_ALL_PROCESSES 63u /* the six discrete processes */
+/* options of the physics list (Table 1's multiple scattering is listed as
+ * "in progress"; the Urban/WentzelVI and Livermore data are not available,
+ * so each option is a published closed form):
+ * MSC: after every e+- step in matter the direction turns by a polar angle
+ *   whose projections are Gaussians of Highland's width (PDG review, Eq.
+ *   34.15) for the pre-step momentum and the step length; no lateral
+ *   displacement.
+ * ANGULAR: bremsstrahlung photons and pair leptons leave at angles of the
+ *   dipole distribution dN/dcos ~ (1 - beta cos)^-2, photoelectrons at
+ *   angles of Sauter's K-shell distribution, instead of along the parent.
+ * RAYLEIGH: coherent photon scattering, Thomson scattering off the atom
+ *   with the form factor of an exponentially screened charge
+ *   (Thomas-Fermi radius); a fourth photon process. */
+#define EMT_MSC 64u
+#define EMT_ANGULAR 128u
+#define EMT_RAYLEIGH 256u
 
 /* step-loop driver of emt_run */
 #define EMT_LOOP_PLAIN 0 /* host loop: one kernel launch and one counter read per step */
@@ -102,6 +118,11 @@ typedef struct emt_options {
     int32_t select_policy;  /* EMT_SELECT_*: which tracks step when more than max_active are in flight */
     int64_t max_active;     /* > 0: at most this many tracks step per iteration, the others are
                                held unchanged (split schedule only); 0: every track steps */
+    int64_t spill_above;    /* > 0 (with LOW_ENERGY selection, >= max_active): held tracks beyond
+                               the spill_above lowest-energy ones move to host memory and come
+                               back when fewer than spill_above/2 remain on the device (the
+                               paper's buffering of secondaries in CPU memory; plain driver);
+                               0: off */
 } emt_options;
 
 /* Track selection (Sec. 4: "preferentially selecting lower-energy particles
@@ -231,6 +252,8 @@ typedef struct emt_run_stats {
                              around each launch, or each graph launch) */
     int32_t kernel_launches;
     int64_t held;         /* track copies held back by the track selection */
+    int64_t spilled;      /* tracks moved to host memory by the host spill */
+    int64_t peak_spilled; /* most tracks in host memory at once */
 } emt_run_stats;
 
 /* Step every track in flight until none is left or max_iterations
@@ -284,7 +307,8 @@ emt_status emt_read_event(emt_ctx* ctx, uint64_t event_id, double* hist, double*
  * ids (host, may be NULL) receives the event ids. */
 emt_status emt_read_all(emt_ctx* ctx, double* hist, double* summary, uint64_t* ids, int32_t where);
 int32_t emt_events_in_flight(const emt_ctx* ctx);
-/* Tracks waiting for their next step (as of the last call). */
+/* Tracks waiting for their next step (as of the last call), including
+ * tracks spilled to host memory. */
 int64_t emt_tracks_in_flight(const emt_ctx* ctx);
 
 /* ---------------------------------------------------------------------
@@ -327,7 +351,8 @@ emt_status emt_serve(emt_ctx* ctx, int32_t n_events, const uint64_t* event_ids, 
  * out[n] (n = grid size).  gamma q: 0 photo, 1 compton, 2 pair;
  * e-: 0 ioni, 1 brems, 3 range; e+: 0 ioni, 1 brems, 2 annih, 3 range;
  * q = 4: restricted stopping power; q = 5: energy grid.  Returns the grid
- * size in *n_out.  Values are FP64 regardless of precision. */
+ * size in *n_out.  Values are FP64 regardless of precision.  gamma q = 3 is
+ * the Rayleigh cross section (zero unless EMT_RAYLEIGH is on). */
 emt_status emt_get_table(emt_ctx* ctx, int32_t m, int32_t p, int32_t q, double* out, int32_t cap, int32_t* n_out);
 
 /* Diagnostics: replace the tracks in flight by explicit track states and

@@ -25,10 +25,11 @@ _lock = threading.Lock()
 _lib = None
 
 # process ids of orc_sample (7, 8: with the angular option)
-PHOTO, COMPTON, PAIR, IONI, BREMS, ANNIH, BHABHA, BREMS_ANGULAR, PAIR_ANGULAR = range(9)
+PHOTO, COMPTON, PAIR, IONI, BREMS, ANNIH, BHABHA, BREMS_ANGULAR, PAIR_ANGULAR, RAYLEIGH, PHOTO_ANGULAR = range(11)
 ALL_PROCESSES = 63
-MSC = 64        # process-mask bit: multiple scattering of e+-
-ANGULAR = 128   # process-mask bit: angular distributions of brems and pair
+MSC = 64          # process-mask bit: multiple scattering of e+-
+ANGULAR = 128     # process-mask bit: angular distributions of brems, pair, photoelectron
+RAYLEIGH_BIT = 256  # process-mask bit: Rayleigh scattering
 
 
 def build(force: bool = False) -> str:
@@ -74,6 +75,8 @@ def lib():
                 "orc_gauss_legendre": (None, [i32, p, p]),
                 "orc_sample": (i32, [i32, d, d, d, u32, u64, u64, u32, p]),
                 "orc_highland": (d, [d, d, d]),
+                "orc_sigma_rayleigh_atom": (d, [d, d]),
+                "orc_dsigma_rayleigh_dx": (d, [d, d, d]),
                 "orc_msc": (i32, [d, d, d, u32, u64, u64, u32, p]),
                 "orc_create": (p, [p, i32, p, p, i32, p, u32]),
                 "orc_destroy": (None, [p]),

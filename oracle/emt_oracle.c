@@ -36,6 +36,8 @@
 #define NAVO 6.02214076e23        /* Avogadro, 1/mol */
 #define PI 3.14159265358979323846
 #define FIELD_C 2.99792458        /* q/p -> curvature: 1/(cm T) per 1/MeV */
+#define BOHR 0.529177210903e-8    /* Bohr radius, cm (CODATA 2018) */
+#define HBARC 197.3269804e-13     /* hbar c, MeV cm (CODATA 2018) */
 #define INF_D (1.0 / 0.0)
 
 /* ------------------------------------------------------------------ */
@@ -304,6 +306,56 @@ double orc_dsigma_heitler_deps(double T, double eps)
  * small y^2/9 term): dSigma/dk = 1/(X0 k) (4/3 - 4/3 y + y^2), y = k/E,
  * E = T + me, k <= T.  Discrete part k in (kc, T]:
  * Sigma = 1/X0 [ 4/3 ln(T/kc) - 4/3 (T-kc)/E + (T^2 - kc^2)/(2E^2) ].   */
+/* Rayleigh (coherent) scattering, process bit ORC_RAYLEIGH (Table 1 uses
+ * Livermore form factors, which are not available): Thomson scattering off
+ * the atom with the form factor of an exponentially screened charge,
+ * F(q) = Z / (1 + (q a)^2)^2, a = 0.88534 a0 Z^(-1/3) (the Thomas-Fermi
+ * radius).  With x = 1 - cos(theta), (q a)^2 = b x, b = 2 (k a / hbar c)^2:
+ * dsigma/dx = pi re^2 Z^2 (1 + (1 - x)^2) / (1 + b x)^4 on [0, 2].
+ * The integral I(b) = int_0^2 (2 - 2x + x^2) (1 + b x)^-4 dx is summed as
+ * its Taylor series below b = 0.1 (the closed form cancels there) and in
+ * closed form above: with y = 1 + b x, Y = 1 + 2 b,
+ * I = [A (1 - Y^-3)/3 + B (1 - Y^-2)/2 + C (1 - Y^-1)] / b,
+ * A = 2 + 2/b + 1/b^2, B = -2/b - 2/b^2, C = 1/b^2. */
+static double rayleigh_b(double Z, double k)
+{
+    double a = 0.88534 * BOHR / cbrt(Z);
+    double y = k * a / HBARC;
+    return 2.0 * y * y;
+}
+
+static double rayleigh_integral(double b)
+{
+    if (b < 0.1) {
+        /* sum_n (-1)^n C(n+3,3) b^n m_n, m_n = int_0^2 (2 - 2x + x^2) x^n dx */
+        double sum = 0.0, bn = 1.0, p2 = 4.0; /* p2 = 2^(n+2) */
+        for (int n = 0; n < 40; ++n) {
+            double mn = p2 / (n + 1.0) - 2.0 * p2 / (n + 2.0) + 2.0 * p2 / (n + 3.0);
+            double c = (n + 1.0) * (n + 2.0) * (n + 3.0) / 6.0;
+            sum += ((n & 1) ? -c : c) * bn * mn;
+            bn *= b;
+            p2 *= 2.0;
+        }
+        return sum;
+    }
+    double Y = 1.0 + 2.0 * b;
+    double A = 2.0 + 2.0 / b + 1.0 / (b * b), B = -2.0 / b - 2.0 / (b * b), C = 1.0 / (b * b);
+    double y1 = 1.0 / Y, y2 = y1 * y1, y3 = y2 * y1;
+    return (A * (1.0 - y3) / 3.0 + B * (1.0 - y2) / 2.0 + C * (1.0 - y1)) / b;
+}
+
+double orc_sigma_rayleigh_atom(double Z, double k)
+{
+    return PI * RE * RE * Z * Z * rayleigh_integral(rayleigh_b(Z, k));
+}
+
+double orc_dsigma_rayleigh_dx(double Z, double k, double x)
+{
+    double b = rayleigh_b(Z, k);
+    double d = 1.0 + b * x;
+    return PI * RE * RE * Z * Z * (2.0 - 2.0 * x + x * x) / (d * d * d * d);
+}
+
 double orc_sigma_brems_macro(double x0_cm, double T, double kc)
 {
     if (T <= kc) return 0.0;
@@ -485,6 +537,7 @@ static void build_tables(orc_handle* h)
                 }
                 tab(h, mi, 0, 2)[i] = s;
             }
+            if (h->mask & ORC_RAYLEIGH) tab(h, mi, 0, 3)[i] = m->n_at * orc_sigma_rayleigh_atom(m->Z, E);
             /* electrons */
             if (h->mask & ORC_IONI) tab(h, mi, 1, 0)[i] = m->n_el * orc_sigma_moller(E, cut_e);
             if (h->mask & ORC_BREMS) tab(h, mi, 1, 1)[i] = orc_sigma_brems_macro(m->x0_cm, E, kc);
@@ -904,7 +957,7 @@ static int momentum_balance(double pa, const double da[3], double pb, const doub
 /* Each writes products: sec_t[k] (type), sec_T[k], sec_dir[k][3].     */
 /* The parent's new energy/direction is returned through *T, dir.      */
 /* ------------------------------------------------------------------ */
-enum { P_PHOTO = 0, P_COMPTON = 1, P_PAIR = 2, P_IONI = 3, P_BREMS = 4, P_ANNIH = 5 };
+enum { P_PHOTO = 0, P_COMPTON = 1, P_PAIR = 2, P_IONI = 3, P_BREMS = 4, P_ANNIH = 5, P_RAYLEIGH = 9 };
 
 /* Every rejection loop accepts its candidate after MAX_TRIALS trials (a
  * safety bound against non-finite input; every acceptance probability here
@@ -970,6 +1023,65 @@ static void sample_compton(draws_t* d, double k, double dir[3], products_t* out,
 
 /* Bethe-Heitler (complete screening): x uniform on [eps0, 1-eps0],
  * accept with 1 - 4/3 x(1-x) (<= 1).  Both leptons along the photon. */
+/* Rayleigh angle: x = 1 - cos(theta) from (1 + b x)^-4 by inversion,
+ * (1 + b x)^-3 = 1 - u (1 - (1 + 2b)^-3) (written with log1p/expm1,
+ * exact for small b), accepted with (1 + (1 - x)^2)/2; the photon keeps its
+ * energy; azimuth 2 pi u. */
+static void sample_rayleigh(draws_t* d, double k, double Z, double dir[3])
+{
+    double b = rayleigh_b(Z, k);
+    double tail = -expm1(-3.0 * log1p(2.0 * b));
+    double x;
+    for (int trial = 1;; ++trial) {
+        double u1 = draw(d), u2 = draw(d);
+        x = expm1(-log1p(-u1 * tail) / 3.0) / b;
+        if (x > 2.0) x = 2.0;
+        if (2.0 * u2 <= 2.0 - 2.0 * x + x * x || trial >= MAX_TRIALS) break;
+    }
+    double phi = 2.0 * PI * draw(d);
+    double out[3];
+    double cost = 1.0 - x;
+    rotate(dir, cost, phi, out);
+    memcpy(dir, out, sizeof out);
+}
+
+/* Photoelectron angle (angular option): Sauter's K-shell distribution,
+ * dN/dcos ~ sin^2(theta) / (1 - beta cos)^4 [1 + g (1 - beta cos)],
+ * g = gamma (gamma - 1) (gamma - 2) / 2.  In v = 1 - beta cos, v in
+ * [a, 2 - a] (a = 1 - beta), the density is f(v) = (v - a)(2 - a - v)
+ * (1 + g v) / v^4, bounded by 16 [(v + a)^-3 + max(g, 0) (v + a)^-2];
+ * both envelope terms invert in closed form.  Returns 1 - cos(theta) =
+ * (v - a)/beta.  Below beta = 1e-3 the direction is isotropic. */
+static double sauter_one_minus_cos(draws_t* d, double T)
+{
+    double E = T + ME;
+    double p = sqrt(T * (T + 2.0 * ME));
+    double beta = p / E;
+    if (!(beta > 1e-3)) return 2.0 * draw(d);
+    double gam = E / ME;
+    double a = ME * ME / (E * (E + p));
+    double g = 0.5 * gam * (gam - 1.0) * (gam - 2.0);
+    double gp = g > 0.0 ? g : 0.0;
+    double i2a = 1.0 / (2.0 * a);
+    double w1 = 0.5 * (i2a * i2a - 0.25), w2 = gp * (i2a - 0.5);
+    double v = a;
+    for (int trial = 1;; ++trial) {
+        double u1 = draw(d), u2 = draw(d), u3 = draw(d);
+        if (u1 * (w1 + w2) < w1) {
+            double w = i2a * i2a * (1.0 - u2) + 0.25 * u2; /* (v + a)^-2 */
+            v = 1.0 / sqrt(w) - a;
+        } else {
+            double w = i2a * (1.0 - u2) + 0.5 * u2; /* (v + a)^-1 */
+            v = 1.0 / w - a;
+        }
+        double va = v + a;
+        double f = (v - a) * (2.0 - a - v) * (1.0 + g * v) / (v * v * v * v);
+        double env = 16.0 * (1.0 / (va * va * va) + gp / (va * va));
+        if (u3 * env <= f || trial >= MAX_TRIALS) break;
+    }
+    return (v - a) / beta;
+}
+
 /* Angular distribution of a lepton or photon emitted by a lepton of
  * kinetic energy T (angular option, process bit ORC_ANGULAR): the dipole
  * form dN/dcos(theta) ~ (1 - beta cos(theta))^-2, whose width is ~1/gamma
@@ -1030,12 +1142,18 @@ static void sample_pair(draws_t* d, double k, const double dir[3], products_t* o
 
 /* photoelectric stand-in: photoelectron T = k - bk along the photon,
  * binding energy bk deposited locally */
-static void sample_photo(double k, double bk, const double dir[3], products_t* out)
+static void sample_photo(draws_t* d, double k, double bk, const double dir[3], products_t* out, int angular)
 {
     out->n = 1;
     out->type[0] = 1;
     out->T[0] = k - bk;
-    for (int a = 0; a < 3; ++a) out->dir[0][a] = dir[a];
+    if (angular) {
+        double omc = sauter_one_minus_cos(d, k - bk);
+        double phi = 2.0 * PI * draw(d);
+        emit_dir(dir, omc, phi, out->dir[0]);
+    } else {
+        for (int a = 0; a < 3; ++a) out->dir[0][a] = dir[a];
+    }
     out->local += bk;
     out->parent_alive = 0;
 }
@@ -1184,7 +1302,9 @@ int orc_sample(int process, double E, double cut_e, double cut_g, uint32_t seed,
     memset(&pr, 0, sizeof pr);
     double Enew = E;
     switch (process) {
-    case P_PHOTO: sample_photo(E, cut_e, dir, &pr); Enew = 0.0; break;
+    case P_PHOTO: sample_photo(&dr, E, cut_e, dir, &pr, 0); Enew = 0.0; break;
+    case 10: sample_photo(&dr, E, cut_e, dir, &pr, 1); Enew = 0.0; break;
+    case P_RAYLEIGH: sample_rayleigh(&dr, E, cut_e, dir); break; /* cut_e carries Z */
     case P_COMPTON: sample_compton(&dr, E, dir, &pr, &Enew); break;
     case P_PAIR: sample_pair(&dr, E, dir, &pr, 0); Enew = 0.0; break;
     case 8: sample_pair(&dr, E, dir, &pr, 1); Enew = 0.0; break;
@@ -1414,14 +1534,17 @@ static void step_track(const orc_handle* h, uint64_t event_id, track_t* tr, tall
     int mi = tr->vol >= 0 ? h->layer_mat[tr->vol] : -1;
     const mat_t* m = (mi >= 0 && mi < h->n_mat && !h->mat[mi].vacuum) ? &h->mat[mi] : NULL;
     int charged = tr->type != 0;
-    double sig[3] = {0.0, 0.0, 0.0};
-    int nproc = tr->type == 2 ? 3 : (tr->type == 1 ? 2 : 3);
+    double sig[4] = {0.0, 0.0, 0.0, 0.0};
+    /* photons: photo, Compton, pair (+ Rayleigh); e-: ioni, brems;
+     * e+: ioni, brems, annihilation */
+    int nproc = tr->type == 2 ? 3 : (tr->type == 1 ? 2 : ((h->mask & ORC_RAYLEIGH) ? 4 : 3));
     double sig_tot = 0.0;
     double R = 0.0;
     if (m) {
         for (int i = 0; i < nproc; ++i) sig[i] = lookup(h, tab(h, mi, tr->type, i), tr->T);
         sig_tot = sig[0] + sig[1];
-        if (nproc == 3) sig_tot = sig_tot + sig[2];
+        if (nproc >= 3) sig_tot = sig_tot + sig[2];
+        if (nproc == 4) sig_tot = sig_tot + sig[3];
     }
     double s_int = INF_D;
     if (sig_tot > 0.0) {
@@ -1524,7 +1647,7 @@ static void step_track(const orc_handle* h, uint64_t event_id, track_t* tr, tall
         }
         int pid; /* physics process id */
         if (tr->type == 0)
-            pid = proc == 0 ? P_PHOTO : (proc == 1 ? P_COMPTON : P_PAIR);
+            pid = proc == 0 ? P_PHOTO : (proc == 1 ? P_COMPTON : (proc == 2 ? P_PAIR : P_RAYLEIGH));
         else
             pid = proc == 0 ? P_IONI : (proc == 1 ? P_BREMS : P_ANNIH);
         res->interacted = 1;
@@ -1538,7 +1661,7 @@ static void step_track(const orc_handle* h, uint64_t event_id, track_t* tr, tall
         switch (pid) {
         case P_PHOTO:
             if (T > m->bk)
-                sample_photo(T, m->bk, tr->u, &pr);
+                sample_photo(&dr, T, m->bk, tr->u, &pr, (h->mask & ORC_ANGULAR) != 0);
             else
                 pr.null_interaction = 1;
             break;
@@ -1569,6 +1692,7 @@ static void step_track(const orc_handle* h, uint64_t event_id, track_t* tr, tall
                 pr.null_interaction = 1;
             break;
         case P_ANNIH: sample_annih(&dr, T, tr->u, &pr); break;
+        case P_RAYLEIGH: sample_rayleigh(&dr, T, m->Z, tr->u); break;
         }
         if (pr.local != 0.0) {
             deposit(h, ta, tr->vol, tr->x[2], pr.local);

@@ -31,7 +31,8 @@ extern "C" {
 #define ORC_BREMS 16u
 #define ORC_ANNIH 32u
 #define ORC_MSC 64u     /* multiple scattering of e+- (Highland width) */
-#define ORC_ANGULAR 128u /* dipole angular distributions for brems and pair */
+#define ORC_ANGULAR 128u /* angular distributions: dipole for brems and pair, Sauter for the photoelectron */
+#define ORC_RAYLEIGH 256u /* Rayleigh scattering (screened-atom form factor) */
 
 typedef struct orc_handle orc_handle;
 
@@ -53,6 +54,8 @@ double orc_dsigma_moller_deps(double T, double eps);
 double orc_sigma_bhabha(double T, double cut);
 double orc_dsigma_bhabha_deps(double T, double eps);
 double orc_sigma_heitler(double T);              /* per electron, cm^2 */
+double orc_sigma_rayleigh_atom(double Z, double k); /* cm^2 per atom */
+double orc_dsigma_rayleigh_dx(double Z, double k, double x); /* per unit x = 1 - cos */
 double orc_dsigma_heitler_deps(double T, double eps);
 double orc_sigma_brems_macro(double x0_cm, double T, double kc); /* 1/cm */
 double orc_dsigma_brems_macro_dk(double x0_cm, double T, double k);
@@ -65,8 +68,9 @@ double orc_dedx_coll(double Z, double A, double rho, double I_eV, int charge,
 void orc_gauss_legendre(int n, double* x, double* w);
 
 /* ---- samplers (single interaction, from a track's draw stream) ---- */
-/* out layout per sampler documented in emt_oracle.c; process 7 and 8 are
- * bremsstrahlung and pair production with the angular option */
+/* out layout per sampler documented in emt_oracle.c; process 7, 8 and 10
+ * are bremsstrahlung, pair production and the photoelectric effect with the
+ * angular option; 9 is Rayleigh scattering (cut_e carries Z) */
 int orc_sample(int process, double E, double cut_e, double cut_g, uint32_t seed,
                uint64_t event_id, uint64_t uid, uint32_t step, double* out);
 /* multiple scattering: Highland width, and the deflection of dir (in

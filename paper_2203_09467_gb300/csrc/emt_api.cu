@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -38,13 +39,16 @@ struct Plan {
     size_t trk[2][11];
     size_t cnt, status, total_steps, done_head, ehist;
     size_t hist, ledger, counts, live, event_id, done_ring;
-    size_t grid, gridf, tab, tabf, dedx, mats, bk, vacuum, scratch;
+    size_t grid, gridf, tab, tabf, dedx, mats, bk, vacuum, x0, ray_a, scratch;
     size_t zb, lmat, lbin;
     size_t st_ev, st_type, st_T, st_pos, st_dir, st_uid, st_slot, st_ids, st_start, st_runs;
     size_t slots_tmp, out_hist, out_summary;
     size_t iq[13];  // split schedule: interaction queue fields
     size_t step_hist;  // [3][step_bins] when step_bins > 0
     int step_bins;
+    size_t spill[11];     // host spill: staging buffer of Q track records (when spill_above > 0)
+    size_t spill_ticket;  // [3]
+    bool spill_on;
     int64_t Q;
     int max_events, hstride, max_prim;
     bool mixed;
@@ -84,6 +88,8 @@ Plan make_plan(const emt_options& o)
     p.mats = p.add(kMaxMat * sizeof(MaterialDev));
     p.bk = p.add(kMaxMat * sizeof(double));
     p.vacuum = p.add(kMaxMat * sizeof(int));
+    p.x0 = p.add(kMaxMat * sizeof(double));
+    p.ray_a = p.add(kMaxMat * sizeof(double));
     p.scratch = p.add((32 + (size_t)kMaxMat * 2 * kMaxGrid) * sizeof(double));
     p.zb = p.add((kMaxLayers + 1) * sizeof(double));
     p.lmat = p.add(kMaxLayers * sizeof(int));
@@ -112,6 +118,9 @@ Plan make_plan(const emt_options& o)
     p.out_summary = p.add(E * EMT_SUMMARY_LEN * sizeof(double));
     p.step_bins = o.step_hist_bins;
     p.step_hist = p.step_bins > 0 ? p.add((size_t)3 * p.step_bins * sizeof(unsigned long long)) : 0;
+    p.spill_on = o.spill_above > 0;
+    for (int f = 0; f < 11; ++f) p.spill[f] = p.spill_on ? p.add(Q * fs[f]) : 0;
+    p.spill_ticket = p.add(3 * sizeof(int));
     return p;
 }
 
@@ -133,6 +142,10 @@ bool valid_options(const emt_options& o, std::string& why)
         return why = "select_policy", false;
     if (o.max_active > 0 && o.schedule != EMT_SCHEDULE_SPLIT)
         return why = "track selection (max_active > 0) needs the split schedule", false;
+    if (o.spill_above < 0) return why = "spill_above must be >= 0", false;
+    if (o.spill_above > 0 &&
+        (o.max_active <= 0 || o.select_policy != EMT_SELECT_LOW_ENERGY || o.spill_above < o.max_active))
+        return why = "host spill needs low-energy track selection with spill_above >= max_active", false;
     return true;
 }
 
@@ -237,6 +250,10 @@ struct emt_ctx {
     // CUDA graph of graph_steps iterations
     cudaGraphExec_t graph = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // host spill: track records moved off the device, one byte vector per
+    // field of the track layout (the most recently spilled at the end)
+    std::vector<char> spill_store[11];
+    int64_t spill_n = 0;
     // per-step records of emt_run_traced (null otherwise)
     emt_step_record* trace = nullptr;
     int32_t trace_cap = 0, trace_n = 0;
@@ -270,23 +287,26 @@ emt_status cuda_fail(emt_ctx* c, cudaError_t e, const char* where)
     } while (0)
 
 template <typename R>
+void fill_side(emt_ctx* c, Tracks<R>& q, const size_t* o)
+{
+    q.x = c->at<double>(o[0]);
+    q.y = c->at<double>(o[1]);
+    q.z = c->at<double>(o[2]);
+    q.ux = c->at<R>(o[3]);
+    q.uy = c->at<R>(o[4]);
+    q.uz = c->at<R>(o[5]);
+    q.T = c->at<R>(o[6]);
+    q.uid = c->at<uint64_t>(o[7]);
+    q.ev = c->at<uint32_t>(o[8]);
+    q.step = c->at<uint32_t>(o[9]);
+    q.tv = c->at<uint32_t>(o[10]);
+}
+
+template <typename R>
 void fill_tracks(emt_ctx* c, Params<R>& p)
 {
-    for (int s = 0; s < 2; ++s) {
-        Tracks<R>& q = p.q[s];
-        const size_t* o = c->plan.trk[s];
-        q.x = c->at<double>(o[0]);
-        q.y = c->at<double>(o[1]);
-        q.z = c->at<double>(o[2]);
-        q.ux = c->at<R>(o[3]);
-        q.uy = c->at<R>(o[4]);
-        q.uz = c->at<R>(o[5]);
-        q.T = c->at<R>(o[6]);
-        q.uid = c->at<uint64_t>(o[7]);
-        q.ev = c->at<uint32_t>(o[8]);
-        q.step = c->at<uint32_t>(o[9]);
-        q.tv = c->at<uint32_t>(o[10]);
-    }
+    if (c->plan.spill_on) fill_side(c, p.spill, c->plan.spill);
+    for (int s = 0; s < 2; ++s) fill_side(c, p.q[s], c->plan.trk[s]);
 }
 
 template <typename R>
@@ -326,6 +346,8 @@ void fill_common(emt_ctx* c, Params<R>& p)
     p.seed = c->opt.seed;
     p.bk = c->at<double>(pl.bk);
     p.vacuum = c->at<int>(pl.vacuum);
+    p.x0 = c->at<double>(pl.x0);
+    p.ray_a = c->at<double>(pl.ray_a);
     p.zb = c->at<double>(pl.zb);
     p.lmat = c->at<int>(pl.lmat);
     p.lbin = c->at<int>(pl.lbin);
@@ -334,6 +356,9 @@ void fill_common(emt_ctx* c, Params<R>& p)
     p.max_active = c->opt.max_active;
     p.select_policy = c->opt.select_policy;
     p.ehist = c->at<unsigned>(pl.ehist);
+    p.spill_above = c->opt.spill_above;
+    p.spill_cap = pl.spill_on ? pl.Q : 0;
+    p.spill_ticket = c->at<int>(pl.spill_ticket);
 }
 
 void drop_graph(emt_ctx* c)
@@ -462,6 +487,50 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
     double kernel_ms = 0.0;
     unsigned long long deferred_prev = def0, held_prev = held0;
     Counters trace_cnt[3];
+    // host spill: field sizes of a track record, and the refill rule (when
+    // fewer than spill_above/2 tracks are on the device, move the most
+    // recently spilled back, up to spill_above in total)
+    const size_t rs = c->mixed() ? 4 : 8;
+    const size_t fs[11] = {8, 8, 8, rs, rs, rs, rs, 8, 4, 4, 4};
+    auto refill = [&]() -> emt_status {
+        const int64_t N = c->live_g + c->live_c;
+        if (c->spill_n == 0 || N >= c->opt.spill_above / 2) return EMT_OK;
+        const int64_t n = std::min<int64_t>(c->spill_n, std::min<int64_t>(c->opt.spill_above - N, pl.Q - 2 - N));
+        if (n <= 0) return EMT_OK;
+        const int64_t first = c->spill_n - n;
+        int64_t ng = 0;
+        const uint32_t* tv = reinterpret_cast<const uint32_t*>(c->spill_store[10].data()) + first;
+        for (int64_t k = 0; k < n; ++k) ng += (tv[k] & 0xFFu) == 0u;
+        for (int f = 0; f < 11; ++f)
+            EMT_CUDA(c, cudaMemcpyAsync(c->pool + pl.spill[f], c->spill_store[f].data() + fs[f] * first, fs[f] * n,
+                                        cudaMemcpyHostToDevice, c->stream));
+        EMT_CUDA(c, Launch<R>::unspill(p, (int)(c->it & 1), (int)(c->it % 3), (int)n, c->stream));
+        EMT_CUDA(c, cudaStreamSynchronize(c->stream));
+        for (int f = 0; f < 11; ++f) c->spill_store[f].resize(fs[f] * first);
+        c->spill_n = first;
+        c->live_g += ng;
+        c->live_c += n - ng;
+        return EMT_OK;
+    };
+    // after a step: move the tracks it spilled to host memory
+    auto move_out = [&](int cin) -> emt_status {
+        int spilled = 0;
+        EMT_CUDA(c, cudaMemcpyAsync(&spilled, c->pool + pl.cnt + sizeof(Counters) * cin + offsetof(Counters, spilled),
+                                    sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        EMT_CUDA(c, cudaStreamSynchronize(c->stream));
+        const int64_t n = std::min<int64_t>(spilled, pl.Q);
+        if (n <= 0) return EMT_OK;
+        for (int f = 0; f < 11; ++f) {
+            c->spill_store[f].resize(fs[f] * (c->spill_n + n));
+            EMT_CUDA(c, cudaMemcpyAsync(c->spill_store[f].data() + fs[f] * c->spill_n, c->pool + pl.spill[f],
+                                        fs[f] * n, cudaMemcpyDeviceToHost, c->stream));
+        }
+        EMT_CUDA(c, cudaStreamSynchronize(c->stream));
+        c->spill_n += n;
+        s.spilled += n;
+        s.peak_spilled = std::max<int64_t>(s.peak_spilled, c->spill_n);
+        return EMT_OK;
+    };
     auto read_counts = [&]() -> emt_status {
         EMT_CUDA(c, cudaMemcpyAsync(c->h_cnt, c->pool + pl.cnt + sizeof(Counters) * (c->it % 3), sizeof(Counters),
                                     cudaMemcpyDeviceToHost, c->stream));
@@ -485,6 +554,10 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
         return EMT_OK;
     };
     auto one_plain = [&]() -> emt_status {
+        if (pl.spill_on) {
+            emt_status r0 = refill();
+            if (r0 != EMT_OK) return r0;
+        }
         int side = (int)(c->it & 1), cin = (int)(c->it % 3), cout = (int)((c->it + 1) % 3),
             cclr = (int)((c->it + 2) % 3);
         int64_t chunks = (c->live_g + c->block - 1) / c->block + (c->live_c + c->block - 1) / c->block;
@@ -504,6 +577,7 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
         const int64_t g0 = c->live_g, c0 = c->live_c;
         const double ms0 = kernel_ms;
         emt_status r = read_counts();
+        if (r == EMT_OK && pl.spill_on) r = move_out(cin);
         if (r != EMT_OK || !c->trace || c->trace_n >= c->trace_cap) return r;
         // per-step record: the input counters of this step hold its
         // interaction count; the step counters give the deferred copies
@@ -523,8 +597,8 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
     };
     int64_t done_it = 0;
     auto budget_left = [&]() { return max_iterations <= 0 || done_it < max_iterations; };
-    if (c->opt.loop_mode == EMT_LOOP_PLAIN || c->trace) {
-        while (c->live_g + c->live_c > 0 && budget_left()) {
+    if (c->opt.loop_mode == EMT_LOOP_PLAIN || c->trace || pl.spill_on) {
+        while ((c->live_g + c->live_c > 0 || c->spill_n > 0) && budget_left()) {
             emt_status r = one_plain();
             if (r != EMT_OK) return r;
             ++done_it;
@@ -586,7 +660,7 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
     s.deferred = (int64_t)(c->steps_seen[1] - def0);
     s.held = (int64_t)(c->steps_seen[2] - held0);
     s.peak_tracks = peak;
-    s.live_tracks = c->live_g + c->live_c;
+    s.live_tracks = c->live_g + c->live_c + c->spill_n;
     s.kernel_ms = kernel_ms;
     // every launch reads its inputs and writes its outputs once; the
     // outputs of one launch are the inputs of the next
@@ -795,6 +869,8 @@ emt_status emt_load_materials(emt_ctx* c, const emt_material* mats, int32_t n, c
     b.e_lo = ph->grid_lo_MeV;
     for (int k = 0; k < 3; ++k) b.cut[k] = ph->cut_MeV[k];
     b.mask = ph->process_mask;
+    b.x0 = c->at<double>(pl.x0);
+    b.ray_a = c->at<double>(pl.ray_a);
     b.grid = c->at<double>(pl.grid);
     b.tab = c->at<double>(pl.tab);
     b.dedx = c->at<double>(pl.dedx);
@@ -818,6 +894,7 @@ emt_status emt_load_materials(emt_ctx* c, const emt_material* mats, int32_t n, c
     c->pd.bpd = c->pf.bpd = ph->bins_per_decade;
     c->pd.log10_lo = c->pf.log10_lo = l10;
     c->pd.step_frac = c->pf.step_frac = ph->step_frac;
+    c->pd.mask = c->pf.mask = ph->process_mask;
     c->pd.final_range = c->pf.final_range = ph->final_range_cm;
     c->pd.step_fracf = c->pf.step_fracf = (float)ph->step_frac;
     c->pd.final_rangef = c->pf.final_rangef = (float)ph->final_range_cm;
@@ -1067,7 +1144,7 @@ emt_status emt_read_all(emt_ctx* c, double* hist, double* summary, uint64_t* ids
 {
     emt_status r = check_ready(c);
     if (r != EMT_OK) return r;
-    if (c->live_g + c->live_c != 0) return fail(c, EMT_ERR_NOT_READY, "tracks still in flight");
+    if (c->live_g + c->live_c + c->spill_n != 0) return fail(c, EMT_ERR_NOT_READY, "tracks still in flight");
     if (where != EMT_HOST && where != EMT_DEVICE) return fail(c, EMT_ERR_INVALID_ARG, "where");
     const Plan& pl = c->plan;
     int n = (int)c->order.size();
@@ -1099,7 +1176,7 @@ emt_status emt_read_all(emt_ctx* c, double* hist, double* summary, uint64_t* ids
 
 int32_t emt_events_in_flight(const emt_ctx* c) { return c ? (int32_t)c->order.size() : 0; }
 
-int64_t emt_tracks_in_flight(const emt_ctx* c) { return c ? c->live_g + c->live_c : 0; }
+int64_t emt_tracks_in_flight(const emt_ctx* c) { return c ? c->live_g + c->live_c + c->spill_n : 0; }
 
 emt_status emt_get_table(emt_ctx* c, int32_t m, int32_t p, int32_t q, double* out, int32_t cap, int32_t* n_out)
 {
@@ -1312,6 +1389,8 @@ extern "C" emt_status emt_transport_static(int32_t device, uint32_t seed, const 
     b.e_lo = ph->grid_lo_MeV;
     for (int k = 0; k < 3; ++k) b.cut[k] = ph->cut_MeV[k];
     b.mask = ph->process_mask;
+    b.x0 = reinterpret_cast<double*>(pool + pl.x0);
+    b.ray_a = reinterpret_cast<double*>(pool + pl.ray_a);
     b.grid = reinterpret_cast<double*>(pool + pl.grid);
     b.tab = reinterpret_cast<double*>(pool + pl.tab);
     b.dedx = reinterpret_cast<double*>(pool + pl.dedx);
@@ -1329,6 +1408,7 @@ extern "C" emt_status emt_transport_static(int32_t device, uint32_t seed, const 
     p.log10_lo = (float)std::log10(ph->grid_lo_MeV);
     p.step_frac = ph->step_frac;
     p.final_range = ph->final_range_cm;
+    p.mask = ph->process_mask;
     p.step_fracf = (float)ph->step_frac;
     p.final_rangef = (float)ph->final_range_cm;
 

@@ -39,6 +39,13 @@ constexpr int kSelectOrder = 0;      // the first max_active tracks of the input
 constexpr int kSelectLowEnergy = 1;  // the max_active tracks of lowest energy
 constexpr int kEBins = 128;          // energy classes: quarter octaves from 2^-16 MeV
 constexpr int kEBase = 112 << 2;     // (FP32 exponent << 2 | two mantissa bits) of class 0
+// physics options (process-mask bits beyond the six discrete processes)
+constexpr unsigned kProcMsc = 64u;      // multiple scattering of e+-
+constexpr unsigned kProcAngular = 128u;  // angles of brems photons, pair leptons, photoelectrons
+constexpr unsigned kProcRayleigh = 256u;  // Rayleigh scattering of photons
+constexpr double kBohr = 0.529177210903e-8;  // Bohr radius, cm (CODATA 2018)
+constexpr double kHbarC = 197.3269804e-13;   // hbar c, MeV cm (CODATA 2018)
+constexpr uint32_t kMscDraw = 1u << 20;  // draw index of the two msc uniforms of a step
 constexpr int kStatusQueueOverflow = 1;
 constexpr int kStatusBadTrack = 2;
 
@@ -47,6 +54,10 @@ __device__ __forceinline__ double mlog(double x) { return log(x); }
 __device__ __forceinline__ float mlog(float x) { return logf(x); }
 __device__ __forceinline__ double mexp(double x) { return exp(x); }
 __device__ __forceinline__ float mexp(float x) { return expf(x); }
+__device__ __forceinline__ double mexpm1(double x) { return expm1(x); }
+__device__ __forceinline__ float mexpm1(float x) { return expm1f(x); }
+__device__ __forceinline__ double mlog1p(double x) { return log1p(x); }
+__device__ __forceinline__ float mlog1p(float x) { return log1pf(x); }
 __device__ __forceinline__ double msqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float msqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double msin(double x) { return sin(x); }
@@ -112,7 +123,7 @@ struct Counters {
     int n_int;     // split schedule: tracks queued for an interaction
     int work_b;    // split schedule: chunk dispenser of the interaction kernel
     int ticket;    // track selection: tickets of the boundary energy class
-    int pad;
+    int spilled;   // host spill: tracks written to the spill buffer
 };
 
 // Split schedule: tracks that interact in a step, queued by the transport
@@ -144,6 +155,9 @@ struct Params {
     float log10_lo;  // log10(grid[0]) for the bin guess
     const double* bk;
     const int* vacuum;
+    const double* x0;     // radiation length per material (cm)
+    const double* ray_a;  // Rayleigh screening radius per material (cm)
+    unsigned mask;     // process mask (physics options: kProcMsc, kProcAngular)
     double cut[3];
     double step_frac, final_range;
     float cutf[3];  // the same in FP32 (mixed path)
@@ -193,6 +207,13 @@ struct Params {
     long long max_active;
     int select_policy;
     unsigned* ehist;
+    // host spill: held tracks beyond the spill_above lowest-energy ones are
+    // written to the spill buffer (spill_cap records) instead of the output,
+    // and the host moves them to its memory (0 = off)
+    long long spill_above;
+    Tracks<R> spill;
+    long long spill_cap;
+    int* spill_ticket;  // tickets of the spill boundary class, [3] rotating
 };
 
 // energy class of a kinetic energy (monotonic in T): the FP32 exponent and
@@ -925,8 +946,131 @@ __device__ __forceinline__ void sample_compton(Draws& d, R k, R dir[3], Products
 
 // Bethe-Heitler, complete screening: x = E(e-)/k uniform on
 // [me/k, 1 - me/k], accepted with 1 - 4/3 x (1 - x); leptons collinear
+// Dipole angular distribution of a particle emitted by a lepton of kinetic
+// energy T (physics option kProcAngular): dN/dcos ~ (1 - beta cos)^-2,
+// sampled by inverting its cumulative distribution,
+// 1 - cos = 2 a (1 - u) / (a + 2 beta u) with a = 1 - beta = me^2/(E(E+p)).
 template <typename R>
-__device__ __forceinline__ void sample_pair(Draws& d, R k, const R dir[3], Products<R>& out)
+__device__ __forceinline__ R dipole_one_minus_cos(R T, R u)
+{
+    const R me = R(kMe);
+    R E = T + me;
+    R p = msqrt(T * (T + R(2) * me));
+    R beta = p / E;
+    R a = me * me / (E * (E + p));
+    return R(2) * a * (R(1) - u) / (a + R(2) * beta * u);
+}
+
+template <typename R>
+__device__ __forceinline__ void emit_dir(const R dir[3], R omc, R phi, R out[3])
+{
+    R cost = R(1) - omc;
+    if (cost < R(-1)) cost = R(-1);
+    rotate(dir, cost, phi, out);
+}
+
+// Rayleigh scattering (physics option kProcRayleigh): Thomson scattering
+// off the atom with the form factor of an exponentially screened charge,
+// F = Z / (1 + (q a)^2)^2, a = 0.88534 a0 Z^(-1/3).  With x = 1 - cos and
+// b = 2 (k a / hbar c)^2 the angle density is (1 + (1 - x)^2) / (1 + b x)^4
+// on [0, 2]: x from (1 + b x)^-4 by inversion, (1 + b x)^-3 = 1 - u (1 -
+// (1 + 2b)^-3) (log1p/expm1 forms, exact for small b), accepted with
+// (1 + (1 - x)^2) / 2.  The photon keeps its energy.
+template <typename R>
+__device__ __forceinline__ void sample_rayleigh(Draws& d, R k, R a_screen, R dir[3])
+{
+    R y = k * a_screen / R(kHbarC);
+    R b = R(2) * y * y;
+    R tail = -mexpm1(R(-3) * mlog1p(R(2) * b));
+    R x;
+    for (int trial = 1;; ++trial) {
+        R u1 = draw<R>(d), u2 = draw<R>(d);
+        x = mexpm1(-mlog1p(-u1 * tail) / R(3)) / b;
+        if (x > R(2)) x = R(2);
+        if (R(2) * u2 <= R(2) - R(2) * x + x * x || trial >= kMaxTrials) break;
+    }
+    R phi = R(2.0 * kPi) * draw<R>(d);
+    R out[3];
+    R cost = R(1) - x;
+    rotate(dir, cost, phi, out);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dir[a] = out[a];
+}
+
+// Photoelectron angle (physics option kProcAngular): Sauter's K-shell
+// distribution, dN/dcos ~ sin^2 / (1 - beta cos)^4 [1 + g (1 - beta cos)],
+// g = gamma (gamma - 1) (gamma - 2) / 2.  In v = 1 - beta cos on [a, 2 - a]
+// (a = 1 - beta) the density f(v) = (v - a)(2 - a - v)(1 + g v) / v^4 is
+// bounded by 16 [(v + a)^-3 + max(g, 0) (v + a)^-2], whose two terms invert
+// in closed form.  Returns 1 - cos = (v - a) / beta; isotropic below beta =
+// 1e-3.
+template <typename R>
+__device__ __forceinline__ R sauter_one_minus_cos(Draws& d, R T)
+{
+    const R me = R(kMe);
+    R E = T + me;
+    R p = msqrt(T * (T + R(2) * me));
+    R beta = p / E;
+    if (!(beta > R(1e-3))) return R(2) * draw<R>(d);
+    R gam = E / me;
+    R a = me * me / (E * (E + p));
+    R g = R(0.5) * gam * (gam - R(1)) * (gam - R(2));
+    R gp = g > R(0) ? g : R(0);
+    R i2a = R(1) / (R(2) * a);
+    R w1 = R(0.5) * (i2a * i2a - R(0.25)), w2 = gp * (i2a - R(0.5));
+    R v = a;
+    for (int trial = 1;; ++trial) {
+        R u1 = draw<R>(d), u2 = draw<R>(d), u3 = draw<R>(d);
+        if (u1 * (w1 + w2) < w1) {
+            R w = i2a * i2a * (R(1) - u2) + R(0.25) * u2;
+            v = R(1) / msqrt(w) - a;
+        } else {
+            R w = i2a * (R(1) - u2) + R(0.5) * u2;
+            v = R(1) / w - a;
+        }
+        R va = v + a;
+        R f = (v - a) * (R(2) - a - v) * (R(1) + g * v) / (v * v * v * v);
+        R env = R(16) * (R(1) / (va * va * va) + gp / (va * va));
+        if (u3 * env <= f || trial >= kMaxTrials) break;
+    }
+    return (v - a) / beta;
+}
+
+// Highland's width of the projected multiple-scattering angle (PDG review
+// "Passage of particles through matter", Eq. 34.15, unit charge) after a
+// path s at kinetic energy T; 0 where its bracket turns negative
+template <typename R>
+__device__ __forceinline__ R highland(R T, R s, R x0)
+{
+    R p = msqrt(T * (T + R(2) * R(kMe)));
+    R beta = p / (T + R(kMe));
+    R t = s / x0;
+    R f = R(1) + R(0.038) * mlog(t / (beta * beta));
+    if (!(f > R(0))) return R(0);
+    return R(13.6) / (beta * p) * msqrt(t) * f;
+}
+
+// multiple scattering at the end of a step: space angle theta0 sqrt(-2 ln
+// u_a) (two Gaussian projections of width theta0), capped at pi, azimuth
+// 2 pi u_b, from draws kMscDraw and kMscDraw + 1 of the step.  Not inlined:
+// the step kernel pays for it only when the option is on.
+template <typename R>
+__device__ __noinline__ void msc_deflect(Draws& d, R T, R s, R x0, R u[3])
+{
+    const R th0 = highland(T, s, x0);
+    if (!(th0 > R(0))) return;
+    d.next = kMscDraw;
+    R ua = draw<R>(d), ub = draw<R>(d);
+    R th = th0 * msqrt(R(-2) * mlog(ua));
+    if (th > R(kPi)) th = R(kPi);
+    R out[3];
+    rotate(u, mcos(th), R(2.0 * kPi) * ub, out);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u[a] = out[a];
+}
+
+template <typename R>
+__device__ __forceinline__ void sample_pair(Draws& d, R k, const R dir[3], Products<R>& out, bool angular)
 {
     const R me = R(kMe);
     R eps0 = me / k;
@@ -947,23 +1091,38 @@ __device__ __forceinline__ void sample_pair(Draws& d, R k, const R dir[3], Produ
     out.T[0] = Tm;
     out.type[1] = 2;
     out.T[1] = Tp;
+    if (angular) {
+        // each lepton at its own dipole angle, azimuths phi and phi + pi
+        R um = draw<R>(d);
+        R phi = R(2.0 * kPi) * draw<R>(d);
+        R up = draw<R>(d);
+        emit_dir(dir, dipole_one_minus_cos(Tm, um), phi, out.dir[0]);
+        emit_dir(dir, dipole_one_minus_cos(Tp, up), phi + R(kPi), out.dir[1]);
+    } else {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        out.dir[0][a] = dir[a];
-        out.dir[1][a] = dir[a];
+        for (int a = 0; a < 3; ++a) {
+            out.dir[0][a] = dir[a];
+            out.dir[1][a] = dir[a];
+        }
     }
     out.parent_alive = false;
 }
 
 // photoelectric stand-in: photoelectron T = k - bk along the photon
 template <typename R>
-__device__ __forceinline__ void sample_photo(R k, R bk, const R dir[3], Products<R>& out)
+__device__ __forceinline__ void sample_photo(Draws& d, R k, R bk, const R dir[3], Products<R>& out, bool angular)
 {
     out.n = 1;
     out.type[0] = 1;
     out.T[0] = k - bk;
+    if (angular) {
+        R omc = sauter_one_minus_cos(d, k - bk);
+        R phi = R(2.0 * kPi) * draw<R>(d);
+        emit_dir(dir, omc, phi, out.dir[0]);
+    } else {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) out.dir[0][a] = dir[a];
+        for (int a = 0; a < 3; ++a) out.dir[0][a] = dir[a];
+    }
     out.local += bk;
     out.parent_alive = false;
 }
@@ -971,7 +1130,8 @@ __device__ __forceinline__ void sample_photo(R k, R bk, const R dir[3], Products
 // bremsstrahlung (Tsai complete screening): k = kc (T/kc)^u, accepted with
 // (4/3 - 4/3 y + y^2) / (4/3), y = k/E; photon along the lepton
 template <typename R>
-__device__ __forceinline__ void sample_brems(Draws& d, R T, R kc, const R dir[3], Products<R>& out, R& Tnew)
+__device__ __forceinline__ void sample_brems(Draws& d, R T, R kc, const R dir[3], Products<R>& out, R& Tnew,
+                                             bool angular)
 {
     R E = T + R(kMe);
     R lr = mlog(T / kc);
@@ -986,8 +1146,16 @@ __device__ __forceinline__ void sample_brems(Draws& d, R T, R kc, const R dir[3]
     out.n = 1;
     out.type[0] = 0;
     out.T[0] = k;
+    if (angular) {
+        // photon at the radiating lepton's dipole angle; the lepton keeps
+        // its direction (the nucleus takes the recoil)
+        R u = draw<R>(d);
+        R phi = R(2.0 * kPi) * draw<R>(d);
+        emit_dir(dir, dipole_one_minus_cos(T, u), phi, out.dir[0]);
+    } else {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) out.dir[0][a] = dir[a];
+        for (int a = 0; a < 3; ++a) out.dir[0][a] = dir[a];
+    }
     Tnew = T - k;
     out.parent_alive = true;
 }

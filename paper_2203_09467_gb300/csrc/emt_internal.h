@@ -13,6 +13,8 @@ struct MaterialDev {
 };
 
 struct TableBuild {
+    double* x0;               // [n_mat] radiation length (cm), 0 for vacuum (optional)
+    double* ray_a;            // [n_mat] Rayleigh screening radius (cm) (optional)
     const MaterialDev* mats;  // device
     int n_mat;
     int n_grid;
@@ -46,6 +48,8 @@ struct Launch {
     static cudaError_t step_split(const Params<R>& p, int side, int cin, int cout, int cclr, int grid_a, int grid_b,
                                   int block, cudaStream_t st);
     static int max_blocks_split(int block, int which);
+    // host spill: append n tracks of the spill buffer to side `side`
+    static cudaError_t unspill(const Params<R>& p, int side, int cs, int n, cudaStream_t st);
 };
 
 }  // namespace emt

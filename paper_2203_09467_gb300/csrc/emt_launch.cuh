@@ -7,6 +7,23 @@
 
 namespace emt {
 
+// the physics options (multiple scattering, angular distributions,
+// Rayleigh) select their own kernel instantiations
+template <typename R>
+static bool extended(const Params<R>& p)
+{
+    return (p.mask & (kProcMsc | kProcAngular | kProcRayleigh)) != 0u;
+}
+
+template <typename R, int BS, int G>
+static void launch_fused(const Params<R>& p, int side, int cin, int cout, int cclr, int grid, cudaStream_t st)
+{
+    if (extended(p))
+        k_step<R, BS, G, true><<<grid, BS, 0, st>>>(p, side, cin, cout, cclr);
+    else
+        k_step<R, BS, G, false><<<grid, BS, 0, st>>>(p, side, cin, cout, cclr);
+}
+
 template <typename R>
 cudaError_t Launch<R>::step(const Params<R>& p, int side, int cin, int cout, int cclr, int grid, int block,
                             cudaStream_t st)
@@ -14,14 +31,14 @@ cudaError_t Launch<R>::step(const Params<R>& p, int side, int cin, int cout, int
     const bool cyl = p.geom == kGeomCylinders;
     if (block == 128) {
         if (cyl)
-            k_step<R, 128, kGeomCylinders><<<grid, 128, 0, st>>>(p, side, cin, cout, cclr);
+            launch_fused<R, 128, kGeomCylinders>(p, side, cin, cout, cclr, grid, st);
         else
-            k_step<R, 128, kGeomLayers><<<grid, 128, 0, st>>>(p, side, cin, cout, cclr);
+            launch_fused<R, 128, kGeomLayers>(p, side, cin, cout, cclr, grid, st);
     } else if (block == 256) {
         if (cyl)
-            k_step<R, 256, kGeomCylinders><<<grid, 256, 0, st>>>(p, side, cin, cout, cclr);
+            launch_fused<R, 256, kGeomCylinders>(p, side, cin, cout, cclr, grid, st);
         else
-            k_step<R, 256, kGeomLayers><<<grid, 256, 0, st>>>(p, side, cin, cout, cclr);
+            launch_fused<R, 256, kGeomLayers>(p, side, cin, cout, cclr, grid, st);
     } else {
         return cudaErrorInvalidValue;
     }
@@ -35,6 +52,14 @@ cudaError_t Launch<R>::admit(const Params<R>& p, int side, int cs, int n, const 
 {
     if (n <= 0) return cudaSuccess;
     k_admit<R><<<(n + 255) / 256, 256, 0, st>>>(p, side, cs, n, ev, type, T, pos, dir, slot_of_event, uid_of);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t Launch<R>::unspill(const Params<R>& p, int side, int cs, int n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_unspill<R><<<(n + 255) / 256, 256, 0, st>>>(p, side, cs, n);
     return cudaGetLastError();
 }
 
@@ -57,22 +82,29 @@ cudaError_t Launch<R>::get_tracks(const Params<R>& p, int side, int nG, int nC, 
     return cudaGetLastError();
 }
 
-// resident blocks per SM, the smaller of the two geometry instantiations
+// resident blocks per SM of the fused kernel, the smallest over its
+// instantiations (geometry kind x physics options)
+template <typename R, int BS>
+static int min_blocks_fused()
+{
+    int n[4] = {0, 0, 0, 0};
+    cudaError_t e[4];
+    e[0] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[0], k_step<R, BS, kGeomLayers, false>, BS, 0);
+    e[1] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[1], k_step<R, BS, kGeomCylinders, false>, BS, 0);
+    e[2] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[2], k_step<R, BS, kGeomLayers, true>, BS, 0);
+    e[3] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[3], k_step<R, BS, kGeomCylinders, true>, BS, 0);
+    int m = 1 << 30;
+    for (int k = 0; k < 4; ++k) {
+        if (e[k] != cudaSuccess) return 1;
+        if (n[k] < m) m = n[k];
+    }
+    return m > 0 ? m : 1;
+}
+
 template <typename R>
 int Launch<R>::max_blocks_per_sm(int block)
 {
-    int n1 = 0, n2 = 0;
-    cudaError_t e1, e2;
-    if (block == 128) {
-        e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_step<R, 128, kGeomLayers>, 128, 0);
-        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, k_step<R, 128, kGeomCylinders>, 128, 0);
-    } else {
-        e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_step<R, 256, kGeomLayers>, 256, 0);
-        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, k_step<R, 256, kGeomCylinders>, 256, 0);
-    }
-    if (e1 != cudaSuccess || e2 != cudaSuccess) return 1;
-    const int n = n1 < n2 ? n1 : n2;
-    return n > 0 ? n : 1;
+    return block == 128 ? min_blocks_fused<R, 128>() : min_blocks_fused<R, 256>();
 }
 
 }  // namespace emt
@@ -81,15 +113,25 @@ int Launch<R>::max_blocks_per_sm(int block)
 
 namespace emt {
 
+template <typename R, int BS, bool S, bool X>
+static void launch_split_x(const Params<R>& p, int side, int cin, int cout, int cclr, int grid_a, int grid_b,
+                           cudaStream_t st)
+{
+    if (p.geom == kGeomCylinders)
+        k_transport<R, BS, kGeomCylinders, S, X><<<grid_a, BS, 0, st>>>(p, side, cin, cout, cclr);
+    else
+        k_transport<R, BS, kGeomLayers, S, X><<<grid_a, BS, 0, st>>>(p, side, cin, cout, cclr);
+    k_interact<R, BS, S, X><<<grid_b, BS, 0, st>>>(p, side, cin, cout);
+}
+
 template <typename R, int BS, bool S>
 static void launch_split(const Params<R>& p, int side, int cin, int cout, int cclr, int grid_a, int grid_b,
                          cudaStream_t st)
 {
-    if (p.geom == kGeomCylinders)
-        k_transport<R, BS, kGeomCylinders, S><<<grid_a, BS, 0, st>>>(p, side, cin, cout, cclr);
+    if (extended(p))
+        launch_split_x<R, BS, S, true>(p, side, cin, cout, cclr, grid_a, grid_b, st);
     else
-        k_transport<R, BS, kGeomLayers, S><<<grid_a, BS, 0, st>>>(p, side, cin, cout, cclr);
-    k_interact<R, BS, S><<<grid_b, BS, 0, st>>>(p, side, cin, cout);
+        launch_split_x<R, BS, S, false>(p, side, cin, cout, cclr, grid_a, grid_b, st);
 }
 
 template <typename R>
@@ -118,23 +160,28 @@ cudaError_t Launch<R>::step_split(const Params<R>& p, int side, int cin, int cou
 template <typename R, int BS>
 static int min_blocks_split(int which)
 {
-    int n[4] = {0, 0, 0, 0};
-    cudaError_t e[4];
+    int n[8];
+    cudaError_t e[8];
+    int k = 0;
     if (which == 0) {
-        e[0] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[0], k_transport<R, BS, kGeomLayers, false>, BS, 0);
-        e[1] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[1], k_transport<R, BS, kGeomCylinders, false>, BS, 0);
-        e[2] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[2], k_transport<R, BS, kGeomLayers, true>, BS, 0);
-        e[3] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[3], k_transport<R, BS, kGeomCylinders, true>, BS, 0);
+        e[k] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[k], k_transport<R, BS, kGeomLayers, false, false>, BS, 0), ++k;
+        e[k] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[k], k_transport<R, BS, kGeomCylinders, false, false>, BS, 0), ++k;
+        e[k] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[k], k_transport<R, BS, kGeomLayers, true, false>, BS, 0), ++k;
+        e[k] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[k], k_transport<R, BS, kGeomCylinders, true, false>, BS, 0), ++k;
+        e[k] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[k], k_transport<R, BS, kGeomLayers, false, true>, BS, 0), ++k;
+        e[k] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[k], k_transport<R, BS, kGeomCylinders, false, true>, BS, 0), ++k;
+        e[k] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[k], k_transport<R, BS, kGeomLayers, true, true>, BS, 0), ++k;
+        e[k] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[k], k_transport<R, BS, kGeomCylinders, true, true>, BS, 0), ++k;
     } else {
-        e[0] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[0], k_interact<R, BS, false>, BS, 0);
-        e[1] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[1], k_interact<R, BS, true>, BS, 0);
-        e[2] = e[3] = cudaSuccess;
-        n[2] = n[3] = n[0];
+        e[k] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[k], k_interact<R, BS, false, false>, BS, 0), ++k;
+        e[k] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[k], k_interact<R, BS, true, false>, BS, 0), ++k;
+        e[k] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[k], k_interact<R, BS, false, true>, BS, 0), ++k;
+        e[k] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[k], k_interact<R, BS, true, true>, BS, 0), ++k;
     }
     int m = 1 << 30;
-    for (int k = 0; k < 4; ++k) {
-        if (e[k] != cudaSuccess) return 1;
-        if (n[k] < m) m = n[k];
+    for (int j = 0; j < k; ++j) {
+        if (e[j] != cudaSuccess) return 1;
+        if (n[j] < m) m = n[j];
     }
     return m > 0 ? m : 1;
 }

@@ -27,12 +27,12 @@ __device__ __forceinline__ uint32_t pack_tvm(int type, int vol, int model)
 // the same random numbers when they do step and no result depends on the
 // policy; both kernels count their outputs' energy classes for the next
 // step's selection.
-template <typename R, int BS, int G, bool S>
+template <typename R, int BS, int G, bool S, bool X>
 __global__ void __launch_bounds__(BS, 512 / BS) k_transport(Params<R> p, int side, int cin, int cout, int cclr)
 {
     __shared__ int s_chunk;
     __shared__ unsigned s_eh[S ? kEBins : 1];
-    __shared__ Selection s_sel;
+    __shared__ Selection s_sel, s_spill;
     constexpr bool select = S;
     if (blockIdx.x == 0 && threadIdx.x == 0) p.cnt[cclr] = Counters{};
     if constexpr (select) {
@@ -41,11 +41,18 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_transport(Params<R> p, int sid
             if (blockIdx.x == 0) p.ehist[(size_t)cclr * kEBins + b] = 0u;
         }
         if (threadIdx.x < 32) {
-            Selection sl;
-            sl.cls = kEBins;
-            sl.quota = 0;
-            if (p.select_policy == kSelectLowEnergy) sl = select_threshold(p, cin, threadIdx.x);
-            if (threadIdx.x == 0) s_sel = sl;
+            Selection sl, sp;
+            sl.cls = sp.cls = kEBins;
+            sl.quota = sp.quota = 0;
+            if (p.select_policy == kSelectLowEnergy) {
+                sl = select_threshold(p, cin, threadIdx.x, p.max_active);
+                if (p.spill_above > 0) sp = select_threshold(p, cin, threadIdx.x, p.spill_above);
+            }
+            if (threadIdx.x == 0) {
+                s_sel = sl;
+                s_spill = sp;
+                if (blockIdx.x == 0) p.spill_ticket[cclr] = 0;
+            }
         }
         __syncthreads();
     }
@@ -71,7 +78,7 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_transport(Params<R> p, int sid
         const bool photon_chunk = chunk < chunksG;
         const long long i = photon_chunk ? (long long)chunk * BS + tid : (long long)(chunk - chunksG) * BS + tid;
         const long long n_here = photon_chunk ? nG : nC;
-        const bool active = i < n_here;
+        bool active = i < n_here;
         const long long src = photon_chunk ? i : Q - nC + i;
 
         TrackReg<R> t;
@@ -87,13 +94,41 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_transport(Params<R> p, int sid
             } else {
                 const int cls = active ? energy_class(est_f(t.T)) : kEBins + 1;
                 held = cls > s_sel.cls && cls <= kEBins;
+                int t1 = -1, t2 = -1;  // tickets in the boundary classes
                 const bool edge = cls == s_sel.cls;
                 const unsigned me = __ballot_sync(0xFFFFFFFFu, edge);
                 if (me) {
                     int base = 0;
                     if (lane == __ffs(me) - 1) base = atomicAdd(&p.cnt[cin].ticket, __popc(me));
                     base = __shfl_sync(0xFFFFFFFFu, base, __ffs(me) - 1);
-                    if (edge) held = base + __popc(me & lanes_below) >= s_sel.quota;
+                    t1 = base + __popc(me & lanes_below);
+                    if (edge) held = t1 >= s_sel.quota;
+                }
+                if (p.spill_above > 0) {
+                    // the held tracks above the spill_above lowest-energy ones
+                    // leave the device
+                    const bool edge2 = cls == s_spill.cls && s_spill.cls != s_sel.cls;
+                    const unsigned m2 = __ballot_sync(0xFFFFFFFFu, edge2);
+                    if (m2) {
+                        int base = 0;
+                        if (lane == __ffs(m2) - 1) base = atomicAdd(&p.spill_ticket[cin], __popc(m2));
+                        base = __shfl_sync(0xFFFFFFFFu, base, __ffs(m2) - 1);
+                        t2 = base + __popc(m2 & lanes_below);
+                    }
+                    if (s_spill.cls == s_sel.cls) t2 = t1;
+                    const bool go = held && (cls > s_spill.cls || (cls == s_spill.cls && t2 >= s_spill.quota));
+                    const unsigned mg = __ballot_sync(0xFFFFFFFFu, go);
+                    if (mg) {
+                        int base = 0;
+                        if (lane == 0) base = atomicAdd(&p.cnt[cin].spilled, __popc(mg));
+                        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+                        const long long k = (long long)base + __popc(mg & lanes_below);
+                        if (go && k < p.spill_cap) {
+                            store_track(p.spill, k, t.x, t.u, t.T, t.uid, t.ev, t.step, t.type, t.vol);
+                            held = false;  // neither stepped nor kept on the device
+                            active = false;
+                        }
+                    }
                 }
             }
             const unsigned mh = __ballot_sync(0xFFFFFFFFu, held);
@@ -103,7 +138,7 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_transport(Params<R> p, int sid
             copy_out(t, o);
         } else if (active) {
             bool alive;
-            model = transport_part<G>(p, t, fx, alive);
+            model = transport_part<G, X>(p, t, fx, alive);
             if (model == kNoInteraction) {
                 finish_step(p, t, alive, fx, o);
                 apply_effects(p, t.ev, t.type, t.step, fx);
@@ -150,7 +185,7 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_transport(Params<R> p, int sid
     }
 }
 
-template <typename R, int BS, bool S>
+template <typename R, int BS, bool S, bool X>
 __global__ void __launch_bounds__(BS, 512 / BS) k_interact(Params<R> p, int side, int cin, int cout)
 {
     __shared__ int s_chunk;
@@ -233,7 +268,7 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_interact(Params<R> p, int side
             fx.col = score_col(p, t.vol, t.x[2]);
             fx.finished = false;
             fx.live_delta = 0;
-            interaction_part(p, t, (int)(tv >> 24), fx, o);
+            interaction_part<X>(p, t, (int)(tv >> 24), fx, o);
             stepped = true;
         }
         if (!unlimited) {

@@ -81,7 +81,8 @@ enum Model : int {
     kBhabha = 4,
     kBrems = 5,
     kAnnih = 6,
-    kNumModels = 7,
+    kRayleigh = 7,
+    kNumModels = 8,
     kNoInteraction = -1
 };
 
@@ -144,7 +145,10 @@ __device__ __forceinline__ void apply_effects(const Params<R>& p, uint32_t ev, i
 //    a null interaction.
 // Returns the model to sample in phase B, or kNoInteraction.  `alive`
 // reports whether the track survives phase A.
-template <int G, typename R>
+// G: geometry kind; X: the physics options (multiple scattering, angular
+// distributions, Rayleigh) may be on (kernels without them carry no code
+// for them)
+template <int G, bool X, typename R>
 __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t, Effects& fx, bool& alive)
 {
     fx.dep = 0.0;
@@ -158,10 +162,12 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
     const int mi = t.vol >= 0 ? p.lmat[t.vol] : -1;
     const bool matter = mi >= 0 && !p.vacuum[mi];
     const bool charged = t.type != 0;
-    const int nproc = t.type == 1 ? 2 : 3;
+    // photons: photo, Compton, pair (+ Rayleigh); e-: ioni, brems; e+: ioni,
+    // brems, annihilation
+    const int nproc = t.type == 1 ? 2 : ((X && t.type == 0 && (p.mask & kProcRayleigh)) ? 4 : 3);
     const R* tab = matter ? p.tab + (size_t)(mi * 3 + t.type) * p.n_grid * kNq : nullptr;
 
-    R sig[3] = {R(0), R(0), R(0)};
+    R sig[4] = {R(0), R(0), R(0), R(0)};
     R sig_tot = R(0);
     R Rng = R(0);
     Lookup<R> lk;
@@ -173,9 +179,15 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
         sig[0] = xs_value(p, tab, lk, 0);
         sig[1] = xs_value(p, tab, lk, 1);
         sig_tot = sig[0] + sig[1];
-        if (nproc == 3) {
+        if (nproc >= 3) {
             sig[2] = xs_value(p, tab, lk, 2);
             sig_tot = sig_tot + sig[2];
+        }
+        if constexpr (X) {
+            if (nproc == 4) {
+                sig[3] = xs_value(p, tab, lk, 3);
+                sig_tot = sig_tot + sig[3];
+            }
         }
     }
     const R kInf = R(__longlong_as_double(0x7FF0000000000000ll));
@@ -266,6 +278,7 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
     fx.col = score_col(p, t.vol, t.x[2]);
 
     alive = true;
+    const R T0 = t.T;
     // 6-7: continuous loss
     if (charged && matter) {
         R r = Rng - from_d<R>(s);
@@ -277,6 +290,11 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
             fx.dep += to_d(t.T) + rest_energy(t.type);
             alive = false;
         }
+    }
+    // 6b: multiple scattering at the post-step point (boundary steps too)
+    if constexpr (X) {
+        if (alive && charged && matter && (p.mask & kProcMsc) && s > 0.0)
+            msc_deflect(dr, T0, from_d<R>(s), from_d<R>(p.x0[mi]), t.u);
     }
     // 8: boundary
     if (alive && boundary) {
@@ -304,6 +322,7 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
     if (t.type == 0) {
         if (proc == 0) return T > from_d<R>(p.bk[mi]) ? kPhoto : kNoInteraction;
         if (proc == 1) return kCompton;
+        if (X && proc == 3) return kRayleigh;
         return T > R(2.0 * kMe) ? kPair : kNoInteraction;
     }
     if (proc == 0) {
@@ -342,10 +361,11 @@ __device__ __forceinline__ void finish_step(const Params<R>& p, TrackReg<R>& t, 
 
 // Phase B: sample model `m` for the post-loss state t (draws 2, 3, ... of
 // the step), then step 10.  Secondaries below their cut deposit on the spot.
-template <typename R>
+template <bool X, typename R>
 __device__ __forceinline__ void interaction_part(const Params<R>& p, TrackReg<R>& t, int m, Effects& fx,
                                                  StepOut<R>& o)
 {
+    const bool angular = X && (p.mask & kProcAngular) != 0u;
     const uint64_t event_id = p.event_id[t.ev];
     Draws dr;
     dr.init(p.seed, event_id, t.uid, t.step);
@@ -357,12 +377,15 @@ __device__ __forceinline__ void interaction_part(const Params<R>& p, TrackReg<R>
     const R T = t.T;
     const R cut_e = pcut(p, 1), kc = pcut(p, 0);
     switch (m) {
-    case kPhoto: sample_photo(T, from_d<R>(p.bk[p.lmat[t.vol]]), t.u, pr); break;
+    case kPhoto: sample_photo(dr, T, from_d<R>(p.bk[p.lmat[t.vol]]), t.u, pr, angular); break;
     case kCompton: sample_compton(dr, T, t.u, pr, t.T); break;
-    case kPair: sample_pair(dr, T, t.u, pr); break;
+    case kPair: sample_pair(dr, T, t.u, pr, angular); break;
     case kMoller: sample_moller(dr, T, cut_e, t.u, pr, t.T); break;
     case kBhabha: sample_bhabha(dr, T, cut_e, t.u, pr, t.T); break;
-    case kBrems: sample_brems(dr, T, kc, t.u, pr, t.T); break;
+    case kBrems: sample_brems(dr, T, kc, t.u, pr, t.T, angular); break;
+    case kRayleigh:
+        if constexpr (X) sample_rayleigh(dr, T, from_d<R>(p.ray_a[p.lmat[t.vol]]), t.u);
+        break;
     default: sample_annih(dr, T, t.u, pr); break;
     }
     if (pr.local != R(0)) fx.dep += to_d(pr.local);
@@ -522,7 +545,7 @@ struct Selection {
 };
 
 template <typename R>
-__device__ __forceinline__ Selection select_threshold(const Params<R>& p, int cin, int lane)
+__device__ __forceinline__ Selection select_threshold(const Params<R>& p, int cin, int lane, long long A)
 {
     const unsigned* h = p.ehist + (size_t)cin * kEBins;
     unsigned c[kEBins / 32];
@@ -538,7 +561,6 @@ __device__ __forceinline__ Selection select_threshold(const Params<R>& p, int ci
         const long long y = __shfl_up_sync(0xFFFFFFFFu, incl, off);
         if (lane >= off) incl += y;
     }
-    const long long A = p.max_active;
     const unsigned reach = __ballot_sync(0xFFFFFFFFu, incl >= A);
     Selection sel;
     sel.cls = kEBins;
@@ -592,7 +614,7 @@ struct Staging {
 // is copied unchanged (its step counter, hence its random stream, is kept).
 // Only interactions make two outputs.  When 2n <= Q every step fits and no
 // token is counted.
-template <typename R, int BS, int G>
+template <typename R, int BS, int G, bool X>
 __global__ void __launch_bounds__(BS, 512 / BS) k_step(Params<R> p, int side, int cin, int cout, int cclr)
 {
     __shared__ int s_chunk;
@@ -638,7 +660,7 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_step(Params<R> p, int side, in
         if (active) {
             load_track(qi, src, t);
             bool alive;
-            model = transport_part<G>(p, t, fx, alive);
+            model = transport_part<G, X>(p, t, fx, alive);
             if (model == kNoInteraction) {
                 finish_step(p, t, alive, fx, o);
                 apply_effects(p, t.ev, t.type, t.step, fx);
@@ -706,7 +728,7 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_step(Params<R> p, int side, in
             fx.col = score_col(p, t.vol, t.x[2]);
             fx.finished = false;
             fx.live_delta = 0;
-            interaction_part(p, t, (int)sg.model[tid], fx, o);
+            interaction_part<X>(p, t, (int)sg.model[tid], fx, o);
             stepped = true;
         }
         if (!unlimited) {
@@ -805,6 +827,38 @@ __global__ void k_admit(Params<R> p, int side, int cs, int n, const int32_t* ev,
             store_track(p.q[side], dst, t.x, t.u, t.T, t.uid, t.ev, t.step, t.type, t.vol);
         }
     }
+}
+
+// Host spill: append n tracks of the spill buffer (records 0..n-1, moved
+// back from host memory) to side `side`, counted in slot `cs`.  Their
+// events still count them as alive.
+template <typename R>
+__global__ void k_unspill(Params<R> p, int side, int cs, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    TrackReg<R> t;
+    const bool have = i < n;
+    if (have) load_track(p.spill, i, t);
+    const unsigned mG = __ballot_sync(0xFFFFFFFFu, have && t.type == 0);
+    const unsigned mC = __ballot_sync(0xFFFFFFFFu, have && t.type != 0);
+    int baseG = 0, baseC = 0;
+    if (lane == 0) {
+        if (mG) baseG = atomicAdd(&p.cnt[cs].n[0], __popc(mG));
+        if (mC) baseC = atomicAdd(&p.cnt[cs].n[1], __popc(mC));
+    }
+    baseG = __shfl_sync(0xFFFFFFFFu, baseG, 0);
+    baseC = __shfl_sync(0xFFFFFFFFu, baseC, 0);
+    if (!have) return;
+    const unsigned below = (1u << lane) - 1u;
+    const long long dst = t.type == 0 ? (long long)baseG + __popc(mG & below)
+                                      : p.Q - 1 - ((long long)baseC + __popc(mC & below));
+    if (dst < 0 || dst >= p.Q) {
+        atomicOr(p.status, kStatusQueueOverflow);
+        return;
+    }
+    store_track(p.q[side], dst, t.x, t.u, t.T, t.uid, t.ev, t.step, t.type, t.vol);
+    atomicAdd(&p.ehist[(size_t)cs * kEBins + energy_class(est_f(t.T))], 1u);
 }
 
 // Diagnostics: write explicit track records into side `side`.

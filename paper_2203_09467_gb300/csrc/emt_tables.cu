@@ -89,6 +89,39 @@ __device__ double sigma_bhabha(double T, double cut)
     return 2.0 * kPi * kRe * kRe * kMe / T * br;
 }
 
+// Rayleigh scattering: Thomson scattering off the atom with the form factor
+// of an exponentially screened charge, F = Z / (1 + (q a)^2)^2, screening
+// radius a = 0.88534 a0 Z^(-1/3).  With x = 1 - cos, b = 2 (k a / hbar c)^2,
+// sigma = pi re^2 Z^2 I(b), I(b) = int_0^2 (2 - 2x + x^2) (1 + b x)^-4 dx:
+// its Taylor series below b = 0.1 (the closed form cancels there), else
+// [A (1 - Y^-3)/3 + B (1 - Y^-2)/2 + C (1 - Y^-1)] / b with Y = 1 + 2b,
+// A = 2 + 2/b + 1/b^2, B = -2/b - 2/b^2, C = 1/b^2 (substituting y = 1 + b x).
+__device__ double rayleigh_screening(double Z) { return 0.88534 * kBohr / cbrt(Z); }
+
+__device__ double sigma_rayleigh_atom(double Z, double k)
+{
+    const double y = k * rayleigh_screening(Z) / kHbarC;
+    const double b = 2.0 * y * y;
+    double I;
+    if (b < 0.1) {
+        double sum = 0.0, bn = 1.0, p2 = 4.0;  // p2 = 2^(n+2)
+        for (int n = 0; n < 40; ++n) {
+            const double mn = p2 / (n + 1.0) - 2.0 * p2 / (n + 2.0) + 2.0 * p2 / (n + 3.0);
+            const double c = (n + 1.0) * (n + 2.0) * (n + 3.0) / 6.0;
+            sum += ((n & 1) ? -c : c) * bn * mn;
+            bn *= b;
+            p2 *= 2.0;
+        }
+        I = sum;
+    } else {
+        const double Y = 1.0 + 2.0 * b;
+        const double A = 2.0 + 2.0 / b + 1.0 / (b * b), B = -2.0 / b - 2.0 / (b * b), C = 1.0 / (b * b);
+        const double y1 = 1.0 / Y, y2 = y1 * y1, y3 = y2 * y1;
+        I = (A * (1.0 - y3) / 3.0 + B * (1.0 - y2) / 2.0 + C * (1.0 - y1)) / b;
+    }
+    return kPi * kRe * kRe * Z * Z * I;
+}
+
 __device__ double sigma_heitler(double T)
 {
     double tau = T / kMe;
@@ -221,6 +254,7 @@ __global__ void k_xs(TableBuild b)
         }
         t0[2] = s;
     }
+    if (mask & kProcRayleigh) t0[3] = n_at * sigma_rayleigh_atom(m.Z, E);
     if (mask & 8u) t1[0] = n_el * sigma_moller(E, cut_e);
     if (mask & 16u) t1[1] = sigma_brems_macro(x0_cm, E, kc);
     b.dedx[(size_t)(mi * 3 + 1) * b.n_grid + n] = dedx_total(m, x0_cm, 1, E, cut_e, kc);
@@ -301,8 +335,18 @@ __global__ void k_to_float(const double* src, float* dst, int n)
 
 }  // namespace
 
+__global__ void k_x0(TableBuild b)
+{
+    const int i = threadIdx.x;
+    if (i >= b.n_mat) return;
+    const MaterialDev& m = b.mats[i];
+    b.x0[i] = m.rho > 0.0 ? x0_gcm2(m.Z, m.A) / m.rho : 0.0;
+    if (b.ray_a) b.ray_a[i] = m.rho > 0.0 ? rayleigh_screening(m.Z) : 0.0;
+}
+
 cudaError_t build_tables(const TableBuild& b, double* scratch, cudaStream_t st)
 {
+    if (b.x0) k_x0<<<1, 32, 0, st>>>(b);
     // scratch: 32 doubles of Gauss-Legendre data + n_mat*2*n_grid interval integrals
     double* glx = scratch;
     double* glw = scratch + 16;

@@ -37,7 +37,7 @@ class Options(ctypes.Structure):
                 ("seed", ctypes.c_uint32),
                 ("cuda_stream", ctypes.c_void_p), ("device_pool", ctypes.c_void_p), ("pool_bytes", ctypes.c_size_t),
                 ("step_hist_bins", ctypes.c_int32), ("select_policy", ctypes.c_int32),
-                ("max_active", ctypes.c_int64)]
+                ("max_active", ctypes.c_int64), ("spill_above", ctypes.c_int64)]
 
 
 class Material(ctypes.Structure):
@@ -85,7 +85,8 @@ class StepRecord(ctypes.Structure):
 class RunStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int64), ("track_steps", ctypes.c_int64), ("peak_tracks", ctypes.c_int64),
                 ("deferred", ctypes.c_int64), ("live_tracks", ctypes.c_int64), ("state_bytes", ctypes.c_int64),
-                ("kernel_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int32), ("held", ctypes.c_int64)]
+                ("kernel_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int32), ("held", ctypes.c_int64),
+                ("spilled", ctypes.c_int64), ("peak_spilled", ctypes.c_int64)]
 
 
 _lib = None
@@ -203,7 +204,7 @@ class Context:
     def __init__(self, *, device: int = 0, precision: str = "fp64", slot_capacity: int = 1 << 22,
                  max_events: int = 10000, max_bins: int = 128, block_size: int = 0, loop_mode: str = "plain",
                  graph_steps: int = 12, seed: int = 1, use_torch_pool: bool = True, schedule: str = "fused",
-                 step_hist_bins: int = 0, max_active: int = 0, select: str = "order"):
+                 step_hist_bins: int = 0, max_active: int = 0, select: str = "order", spill_above: int = 0):
         import torch
         L = lib()
         self._torch = torch
@@ -222,6 +223,7 @@ class Context:
         o.step_hist_bins = int(step_hist_bins)
         o.max_active = int(max_active)
         o.select_policy = SELECT[select]
+        o.spill_above = int(spill_above)
         self.device = torch.device("cuda", device)
         self.stream = torch.cuda.Stream(device=self.device)
         o.cuda_stream = ctypes.c_void_p(self.stream.cuda_stream)

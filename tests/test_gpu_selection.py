@@ -83,3 +83,26 @@ def test_low_energy_first_needs_fewer_slots(emt):
           f"iterations {st_all['iterations']}, {st_ord['iterations']}, {st_low['iterations']}")
     assert peak(r_low) < peak(r_ord)
     assert peak(r_low) < peak(r_all)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_host_spill_changes_no_result(emt, precision):
+    """The paper's buffering of pending tracks in CPU memory: with a device
+    budget of 1,100 tracks, held tracks of the highest energies move to host
+    memory and come back later; every result equals the unlimited run's,
+    and the tracks on the device never exceed the budget plus one step's
+    growth."""
+    s = W.calo_setup()
+    n = 60
+    prim = W.calo_primaries(n, energy=5000.0)
+    h0, s0, st0, r0 = traced(emt, s, prim, n, precision=precision)
+    A, D = 1000, 1100
+    h1, s1, st1, r1 = traced(emt, s, prim, n, precision=precision, max_active=A, select="low_energy",
+                             spill_above=D)
+    assert st1["spilled"] > 0 and st1["live_tracks"] == 0
+    N = r1[:, 0] + r1[:, 1]
+    assert N.max() <= D + A, (N.max(), (r0[:, 0] + r0[:, 1]).max())
+    assert np.array_equal(s1[:, 4:], s0[:, 4:])
+    e_in = s0[:, 3]
+    assert np.max(np.abs(s1[:, :3] - s0[:, :3]).max(1) / e_in) <= TOL
+    assert np.max(np.abs(h1 - h0).max(1) / e_in) <= TOL
