@@ -39,16 +39,22 @@ from paper_2203_09467_gb300 import workloads as W  # noqa: E402
 
 METRIC = "track-steps/s"
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the step
-# kernels per track-step, from one ncu capture of every k_transport and
-# k_interact launch of a smaller run of the same workload (the summary and
-# the command are in profiles/).  It is reported only while the kernel
-# sources are the ones that were measured (their SHA-256 below).
+# Per track-step figures of the step kernels from one ncu capture of every
+# k_transport and k_interact launch of a smaller run of the same workload
+# (the summary and the command are in profiles/): DRAM traffic
+# (dram__bytes_read.sum + dram__bytes_write.sum) and FP64-pipe work
+# (sm__thread_inst_executed_pipe_fp64_pred_on.sum, the kernels' FP64
+# arithmetic as compiled: nothing is recomputed).  They are reported only
+# while the kernel sources are the ones that were measured (SHA-256 below).
 TRAFFIC = {
-    "kernel_sha256": "c54e181b34f9681d0fdf7fb6b0920b31255839c339262ed1b18849fbae1e02c7",
-    "bytes_per_track_step": {"calo/fp64": 101.88, "calo/mixed": 79.23},
+    "kernel_sha256": "2c32c17f025de9925db2428ebd6686c3cf76713e3c3c8dd177c5f3bf06e83aa8",
+    "bytes_per_track_step": {"calo/fp64": 102.77, "calo/mixed": 79.31},
+    "fp64_inst_per_track_step": {"calo/fp64": 123.87, "calo/mixed": 28.20},
     "source": "profiles/step_kernels_calo_dram_traffic.md",
 }
+# FP64 pipe peak: 1.25 TFLOP/s nominal FP64 on GB300 (an FMA counts two
+# flops) = 625 G FP64 thread-instructions/s (152 SMs x 2 per clock x ~2.06 GHz)
+FP64_PEAK_GINST = 625.0
 KERNEL_SOURCES = ["emt_device.cuh", "emt_step.cuh", "emt_split.cuh", "emt_launch.cuh", "emt_kernels_fp64.cu",
                   "emt_kernels_mixed.cu"]
 
@@ -337,21 +343,39 @@ def gpu_arm(args):
             "launches": kern_launch, "mean_launch_ms": kern_ms / max(kern_launch, 1),
             "algorithmic_bytes_per_launch": state_bytes / max(kern_launch, 1),
             "kernel_share_of_step": kern_ms / total_ms}
-    per_step = TRAFFIC["bytes_per_track_step"].get(f"{args.workload}/{args.precision}")
+    key = f"{args.workload}/{args.precision}"
+    current = TRAFFIC["kernel_sha256"] == kernel_sha256()
+    per_step = TRAFFIC["bytes_per_track_step"].get(key) if current else None
+    steps_per_launch = steps_done / max(kern_launch, 1)
     if args.traffic_per_launch:
         roof["traffic"] = args.traffic_per_launch
-    elif per_step and TRAFFIC["kernel_sha256"] == kernel_sha256():
-        roof["traffic"] = per_step * steps_done / max(kern_launch, 1)
+    elif per_step:
+        roof["traffic"] = per_step * steps_per_launch
         roof["traffic_source"] = (f"{TRAFFIC['source']}: {per_step:.1f} B per track-step x "
-                                  f"{steps_done / max(kern_launch, 1):.0f} track-steps per launch")
+                                  f"{steps_per_launch:.0f} track-steps per launch")
+    inst = TRAFFIC["fp64_inst_per_track_step"].get(key) if current else None
+    roof_hbm = None
+    if inst:
+        # the step kernels are bound by the FP64 pipe: report that roofline,
+        # and the HBM one beside it
+        roof_hbm = roof
+        ach = inst * steps_done / (kern_ms / 1e3) / 1e9
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GINST, "unit": "G FP64 inst/s",
+                "frac": ach / FP64_PEAK_GINST, "traffic": roof_hbm["traffic"],
+                "peak_source": "nominal 1.25 TFLOP/s FP64 of GB300 = 625 G FP64 thread-instructions/s",
+                "kernel": roof_hbm["kernel"], "launches": kern_launch,
+                "mean_launch_ms": kern_ms / max(kern_launch, 1),
+                "algorithmic_fp64_inst_per_launch": inst * steps_per_launch,
+                "fp64_inst_per_track_step": inst, "kernel_share_of_step": kern_ms / total_ms}
 
     # the plain form: the same events submitted and run one at a time
     forms = None
     if args.one_at_a_time > 0 and rank == 0:
         k = min(args.one_at_a_time, n)
+        # one launch per step (the fused schedule) suits a single event best
         single = emt.context_for(setup, device=local, precision=args.precision, slot_capacity=1 << 22,
                                  max_events=1, block_size=cfg["block_size"], loop_mode="plain",
-                                 schedule=cfg.get("schedule", "split"))
+                                 schedule="fused")
         # primaries of event e: [first[e], first[e + 1]) (grouped by event)
         first = np.searchsorted(prim["event"], np.arange(n + 1))
         steps1 = 0
@@ -400,6 +424,8 @@ def gpu_arm(args):
         "roofline": roof,
         "clocks": clk,
     }
+    if roof_hbm:
+        line["roofline_hbm"] = roof_hbm
     if forms:
         line["forms"] = forms
     if tune:
