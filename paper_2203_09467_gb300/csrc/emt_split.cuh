@@ -27,8 +27,19 @@ __device__ __forceinline__ uint32_t pack_tvm(int type, int vol, int model)
 // the same random numbers when they do step and no result depends on the
 // policy; both kernels count their outputs' energy classes for the next
 // step's selection.
+// Resident threads per SM the transport kernel is compiled for (its
+// register budget): measured on GB300, the FP64 kernel runs fastest with 768
+// (80 registers, a few hundred bytes of spills, 50% more warps to hide the
+// FP64 pipe's latency than with 512), the mixed kernel with 640.
+template <typename R>
+constexpr int transport_threads_per_sm()
+{
+    return sizeof(R) == 8 ? 768 : 640;
+}
+
 template <typename R, int BS, int G, bool S, bool X>
-__global__ void __launch_bounds__(BS, 512 / BS) k_transport(Params<R> p, int side, int cin, int cout, int cclr)
+__global__ void __launch_bounds__(BS, transport_threads_per_sm<R>() / BS)
+    k_transport(Params<R> p, int side, int cin, int cout, int cclr)
 {
     __shared__ int s_chunk;
     __shared__ unsigned s_eh[S ? kEBins : 1];
