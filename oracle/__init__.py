@@ -32,15 +32,25 @@ ANGULAR = 128     # process-mask bit: angular distributions of brems, pair, phot
 RAYLEIGH_BIT = 256  # process-mask bit: Rayleigh scattering
 
 
+def _stale() -> bool:
+    return (not os.path.exists(_LIB)) or any(os.path.getmtime(s) > os.path.getmtime(_LIB) for s in (_SRC, _HDR))
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no FMA contraction, no fast-math)."""
-    stale = (not os.path.exists(_LIB)) or force or any(
-        os.path.getmtime(s) > os.path.getmtime(_LIB) for s in (_SRC, _HDR))
-    if stale:
-        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-               "-pthread", "-std=c11", "-Wall", "-o", _LIB + ".tmp", _SRC, "-lm"]
-        subprocess.check_call(cmd)
-        os.replace(_LIB + ".tmp", _LIB)
+    """Compile the oracle with gcc (no FMA contraction, no fast-math).
+    Concurrent callers (processes of a multi-rank test) serialise on a lock
+    file and write distinct temporaries."""
+    if not (force or _stale()):
+        return _LIB
+    import fcntl
+    with open(_LIB + ".lock", "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        if force or _stale():
+            tmp = f"{_LIB}.{os.getpid()}.tmp"
+            cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                   "-pthread", "-std=c11", "-Wall", "-o", tmp, _SRC, "-lm"]
+            subprocess.check_call(cmd)
+            os.replace(tmp, _LIB)
     return _LIB
 
 

@@ -478,6 +478,8 @@ struct orc_handle {
     double step_frac, final_range;
     unsigned mask;
     double* grid;  /* n_grid */
+    double* igrid; /* n_grid: 1 / (grid[i+1] - grid[i]) (last entry unused) */
+    double* irs;   /* [mat][particle 3][n_grid]: 1 / (R[i+1] - R[i]) of the range tables */
     double* table; /* [mat][particle 3][q NQ][n_grid] */
     /* geometry */
     int n_layers;
@@ -516,6 +518,7 @@ static void build_tables(orc_handle* h)
 {
     int n = h->n_grid;
     for (int i = 0; i < n; ++i) h->grid[i] = h->e_lo * pow(10.0, (double)i / h->bpd);
+    for (int i = 0; i + 1 < n; ++i) h->igrid[i] = 1.0 / (h->grid[i + 1] - h->grid[i]);
     double glx[16], glw[16];
     orc_gauss_legendre(16, glx, glw);
     for (int mi = 0; mi < h->n_mat; ++mi) {
@@ -589,6 +592,8 @@ static void build_tables(orc_handle* h)
                 }
                 R[i] = R[i - 1] + acc;
             }
+            double* irs = h->irs + ((size_t)mi * 3 + p) * n;
+            for (int i = 0; i + 1 < n; ++i) irs[i] = 1.0 / (R[i + 1] - R[i]);
         }
     }
 }
@@ -602,13 +607,16 @@ static int find_bin(const orc_handle* h, double E)
     return n;
 }
 
-/* piecewise linear in E between nodes; constant outside the grid */
+/* piecewise linear in E between nodes; constant outside the grid.  The
+ * fraction within an interval is (E - E_n) times the interval's reciprocal
+ * width, rounded once when the grid is built (a reading: the paper fixes no
+ * interpolation arithmetic; a product instead of a quotient per lookup). */
 static double lookup(const orc_handle* h, const double* v, double E)
 {
     if (E <= h->grid[0]) return v[0];
     if (E >= h->grid[h->n_grid - 1]) return v[h->n_grid - 1];
     int n = find_bin(h, E);
-    double f = (E - h->grid[n]) / (h->grid[n + 1] - h->grid[n]);
+    double f = (E - h->grid[n]) * h->igrid[n];
     return v[n] + (v[n + 1] - v[n]) * f;
 }
 
@@ -618,19 +626,22 @@ static double range_of(const orc_handle* h, const double* R, double T)
 {
     if (T < h->grid[0]) return R[0] * (T / h->grid[0]);
     int n = find_bin(h, T);
-    double f = (T - h->grid[n]) / (h->grid[n + 1] - h->grid[n]);
+    double f = (T - h->grid[n]) * h->igrid[n];
     return R[n] + (R[n + 1] - R[n]) * f;
 }
 
-/* exact inverse of range_of */
-static double inv_range_of(const orc_handle* h, const double* R, double r)
+/* inverse of range_of (the same piecewise-linear function, inverted with
+ * the range intervals' reciprocal widths irs) */
+static double inv_range_of(const orc_handle* h, const double* R, const double* irs, double r)
 {
     if (r < R[0]) return h->grid[0] * (r / R[0]);
     int n = 0;
     while (n + 1 < h->n_grid - 1 && R[n + 1] <= r) ++n;
-    double f = (r - R[n]) / (R[n + 1] - R[n]);
+    double f = (r - R[n]) * irs[n];
     return h->grid[n] + (h->grid[n + 1] - h->grid[n]) * f;
 }
+
+static const double* irs_of(const orc_handle* h, int m, int p) { return h->irs + ((size_t)m * 3 + p) * h->n_grid; }
 
 double orc_range(const orc_handle* h, int m, int ci, double T)
 {
@@ -639,7 +650,7 @@ double orc_range(const orc_handle* h, int m, int ci, double T)
 
 double orc_inv_range(const orc_handle* h, int m, int ci, double r)
 {
-    return inv_range_of(h, tab(h, m, ci, 3), r);
+    return inv_range_of(h, tab(h, m, ci, 3), irs_of(h, m, ci), r);
 }
 
 orc_handle* orc_create(const double* materials, int n_mat, const double* physics, const double* layers,
@@ -673,6 +684,8 @@ orc_handle* orc_create(const double* materials, int n_mat, const double* physics
     h->mask = (unsigned)physics[8];
     h->n_grid = (int)floor(h->bpd * log10(h->e_hi / h->e_lo) + 0.5) + 1;
     h->grid = (double*)malloc(sizeof(double) * h->n_grid);
+    h->igrid = (double*)calloc((size_t)h->n_grid, sizeof(double));
+    h->irs = (double*)calloc((size_t)(n_mat > 0 ? n_mat : 1) * 3 * h->n_grid, sizeof(double));
     h->table = (double*)calloc((size_t)(n_mat > 0 ? n_mat : 1) * 3 * NQ * h->n_grid, sizeof(double));
     h->n_layers = n_layers;
     h->zb[0] = world[0];
@@ -712,6 +725,8 @@ void orc_destroy(orc_handle* h)
 {
     if (!h) return;
     free(h->grid);
+    free(h->igrid);
+    free(h->irs);
     free(h->table);
     free(h);
 }
@@ -1607,7 +1622,7 @@ static void step_track(const orc_handle* h, uint64_t event_id, track_t* tr, tall
     const double T0 = tr->T;
     if (charged && m) {
         double r = R - s;
-        double Tn = r > 0.0 ? inv_range_of(h, tab(h, mi, tr->type, 3), r) : 0.0;
+        double Tn = r > 0.0 ? inv_range_of(h, tab(h, mi, tr->type, 3), irs_of(h, mi, tr->type), r) : 0.0;
         double ed = tr->T - Tn;
         deposit(h, ta, tr->vol, tr->x[2], ed);
         res->edep += ed;

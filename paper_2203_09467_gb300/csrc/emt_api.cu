@@ -39,7 +39,7 @@ struct Plan {
     size_t trk[2][11];
     size_t cnt, status, total_steps, done_head, ehist;
     size_t hist, ledger, counts, live, event_id, done_ring;
-    size_t grid, gridf, tab, tabf, dedx, mats, bk, vacuum, x0, ray_a, scratch;
+    size_t grid, gridf, igrid, igridf, irs, irsf, tab, tabf, dedx, mats, bk, vacuum, x0, ray_a, scratch;
     size_t zb, lmat, lbin;
     size_t st_ev, st_type, st_T, st_pos, st_dir, st_uid, st_slot, st_ids, st_start, st_runs;
     size_t slots_tmp, out_hist, out_summary;
@@ -82,6 +82,10 @@ Plan make_plan(const emt_options& o)
     p.done_ring = p.add(E * sizeof(unsigned));
     p.grid = p.add(kMaxGrid * sizeof(double));
     p.gridf = p.add(kMaxGrid * sizeof(float));
+    p.igrid = p.add(kMaxGrid * sizeof(double));
+    p.igridf = p.add(kMaxGrid * sizeof(float));
+    p.irs = p.add((size_t)kMaxMat * 3 * kMaxGrid * sizeof(double));
+    p.irsf = p.add((size_t)kMaxMat * 3 * kMaxGrid * sizeof(float));
     p.tab = p.add((size_t)kMaxMat * 3 * kMaxGrid * kNq * sizeof(double));
     p.tabf = p.add((size_t)kMaxMat * 3 * kMaxGrid * kNq * sizeof(float));
     p.dedx = p.add((size_t)kMaxMat * 3 * kMaxGrid * sizeof(double));
@@ -876,6 +880,10 @@ emt_status emt_load_materials(emt_ctx* c, const emt_material* mats, int32_t n, c
     b.dedx = c->at<double>(pl.dedx);
     b.tabf = c->mixed() ? c->at<float>(pl.tabf) : nullptr;
     b.gridf = c->mixed() ? c->at<float>(pl.gridf) : nullptr;
+    b.igrid = c->at<double>(pl.igrid);
+    b.irs = c->at<double>(pl.irs);
+    b.igridf = c->mixed() ? c->at<float>(pl.igridf) : nullptr;
+    b.irsf = c->mixed() ? c->at<float>(pl.irsf) : nullptr;
     EMT_CUDA(c, build_tables(b, c->at<double>(pl.scratch), c->stream));
     EMT_CUDA(c, cudaStreamSynchronize(c->stream));
     c->n_mat = n;
@@ -890,6 +898,10 @@ emt_status emt_load_materials(emt_ctx* c, const emt_material* mats, int32_t n, c
     c->pd.tab = b.tab;
     c->pf.grid = c->at<float>(pl.gridf);
     c->pf.tab = c->at<float>(pl.tabf);
+    c->pd.igrid = b.igrid;
+    c->pd.irs = b.irs;
+    c->pf.igrid = c->at<float>(pl.igridf);
+    c->pf.irs = c->at<float>(pl.irsf);
     c->pd.n_grid = c->pf.n_grid = n_grid;
     c->pd.bpd = c->pf.bpd = ph->bins_per_decade;
     c->pd.log10_lo = c->pf.log10_lo = l10;
@@ -1396,6 +1408,10 @@ extern "C" emt_status emt_transport_static(int32_t device, uint32_t seed, const 
     b.dedx = reinterpret_cast<double*>(pool + pl.dedx);
     b.tabf = nullptr;
     b.gridf = nullptr;
+    b.igrid = reinterpret_cast<double*>(pool + pl.igrid);
+    b.irs = reinterpret_cast<double*>(pool + pl.irs);
+    b.igridf = nullptr;
+    b.irsf = nullptr;
     if (build_tables(b, reinterpret_cast<double*>(pool + pl.scratch), st) != cudaSuccess) return EMT_ERR_CUDA;
     for (int k = 0; k < 3; ++k) {
         p.cut[k] = ph->cut_MeV[k];
@@ -1403,6 +1419,8 @@ extern "C" emt_status emt_transport_static(int32_t device, uint32_t seed, const 
     }
     p.grid = b.grid;
     p.tab = b.tab;
+    p.igrid = b.igrid;
+    p.irs = b.irs;
     p.n_grid = n_grid;
     p.bpd = ph->bins_per_decade;
     p.log10_lo = (float)std::log10(ph->grid_lo_MeV);

@@ -150,6 +150,8 @@ struct Params {
     // tables: tab[((m * 3 + p) * n_grid + node) * 4 + q]
     const R* grid;
     const R* tab;
+    const R* igrid;  // 1 / (grid[n+1] - grid[n])
+    const R* irs;    // [(m * 3 + p) * n_grid + n]: 1 / (R[n+1] - R[n]) of the range tables
     int n_grid;
     int bpd;
     float log10_lo;  // log10(grid[0]) for the bin guess
@@ -400,7 +402,7 @@ __device__ __forceinline__ Lookup<R> locate_energy(const Params<R>& p, R E)
         return l;
     }
     l.n = find_bin(p, E);
-    l.f = (E - p.grid[l.n]) / (p.grid[l.n + 1] - p.grid[l.n]);
+    l.f = (E - p.grid[l.n]) * p.igrid[l.n];  // the reciprocal width, rounded once
     return l;
 }
 
@@ -421,23 +423,23 @@ __device__ __forceinline__ R range_value(const Params<R>& p, const R* t, R T, co
     if (T < p.grid[0]) return t[3] * (T / p.grid[0]);
     int n = l.n;
     R f = l.f;
-    if (l.clamp > 0) f = (T - p.grid[n]) / (p.grid[n + 1] - p.grid[n]);
+    if (l.clamp > 0) f = (T - p.grid[n]) * p.igrid[n];
     R a = t[n * kNq + 3], b = t[(n + 1) * kNq + 3];
     return a + (b - a) * f;
 }
 
-// exact inverse of range_value; nstart = bin of the pre-step energy
-// (the answer lies at or below it because r <= R(T))
+// inverse of range_value with the range intervals' reciprocal widths irs;
+// nstart = bin of the pre-step energy (the answer lies at or below it
+// because r <= R(T))
 template <typename R>
-__device__ __forceinline__ R inv_range(const Params<R>& p, const R* t, R r, int nstart)
+__device__ __forceinline__ R inv_range(const Params<R>& p, const R* t, const R* irs, R r, int nstart)
 {
     if (r < t[3]) return p.grid[0] * (r / t[3]);
     int n = nstart;
     while (n > 0 && !le_pos(t[n * kNq + 3], r)) --n;
     int top = p.n_grid - 2;
     while (n < top && le_pos(t[(n + 1) * kNq + 3], r)) ++n;
-    R a = t[n * kNq + 3], b = t[(n + 1) * kNq + 3];
-    R f = (r - a) / (b - a);
+    R f = (r - t[n * kNq + 3]) * irs[n];
     return p.grid[n] + (p.grid[n + 1] - p.grid[n]) * f;
 }
 

@@ -27,6 +27,10 @@ struct TableBuild {
     double* dedx;  // [n_mat][3][n_grid]
     float* tabf;   // optional float copies (mixed precision)
     float* gridf;
+    double* igrid;  // [n_grid] 1 / (grid[n+1] - grid[n]) (last entry 0)
+    double* irs;    // [n_mat][3][n_grid] 1 / (R[n+1] - R[n]) of the range tables
+    float* igridf;  // optional float copies
+    float* irsf;
 };
 
 // scratch: (32 + n_mat * 2 * n_grid) doubles

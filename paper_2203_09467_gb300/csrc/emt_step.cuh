@@ -282,7 +282,7 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
     // 6-7: continuous loss
     if (charged && matter) {
         R r = Rng - from_d<R>(s);
-        R Tn = r > R(0) ? inv_range(p, tab, r, lk.n) : R(0);
+        R Tn = r > R(0) ? inv_range(p, tab, p.irs + (size_t)(mi * 3 + t.type) * p.n_grid, r, lk.n) : R(0);
         R ed = t.T - Tn;
         fx.dep += to_d(ed);
         t.T = Tn;

@@ -335,6 +335,24 @@ __global__ void k_to_float(const double* src, float* dst, int n)
 
 }  // namespace
 
+// reciprocal interval widths of the energy grid and of the range tables
+// (interpolation fractions are products with them, as in the oracle)
+__global__ void k_reciprocals(TableBuild b)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = b.n_grid;
+    if (idx < n) b.igrid[idx] = idx + 1 < n ? 1.0 / (b.grid[idx + 1] - b.grid[idx]) : 0.0;
+    if (idx >= b.n_mat * 3 * n) return;
+    const int row = idx / n, i = idx % n;
+    const int p = row % 3;
+    double v = 0.0;
+    if (p > 0 && i + 1 < n && b.mats[row / 3].rho > 0.0) {
+        const double* t = b.tab + (size_t)row * n * kNq;
+        v = 1.0 / (t[(i + 1) * kNq + 3] - t[i * kNq + 3]);
+    }
+    b.irs[idx] = v;
+}
+
 __global__ void k_x0(TableBuild b)
 {
     const int i = threadIdx.x;
@@ -358,10 +376,14 @@ cudaError_t build_tables(const TableBuild& b, double* scratch, cudaStream_t st)
     int ni = b.n_mat * 2 * b.n_grid;
     k_range_intervals<<<(ni + 127) / 128, 128, 0, st>>>(b, glx, glw, acc);
     k_range_scan<<<1, 64, 0, st>>>(b, acc);
+    const int nr = b.n_mat * 3 * b.n_grid;
+    k_reciprocals<<<(nr + 127) / 128, 128, 0, st>>>(b);
     if (b.tabf) {
         int nt = b.n_mat * 3 * b.n_grid * kNq;
         k_to_float<<<(nt + 255) / 256, 256, 0, st>>>(b.tab, b.tabf, nt);
         k_to_float<<<(b.n_grid + 255) / 256, 256, 0, st>>>(b.grid, b.gridf, b.n_grid);
+        k_to_float<<<(b.n_grid + 255) / 256, 256, 0, st>>>(b.igrid, b.igridf, b.n_grid);
+        k_to_float<<<(nr + 255) / 256, 256, 0, st>>>(b.irs, b.irsf, nr);
     }
     return cudaGetLastError();
 }

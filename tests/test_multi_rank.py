@@ -55,6 +55,8 @@ def test_partition_balances_cost():
 
 
 def test_two_gloo_ranks_equal_single_run(tmp_path):
+    import oracle
+    oracle.build()  # once, before the ranks start
     world = 2
     mp.spawn(_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
     s, prim, ids = _setup()
