@@ -47,9 +47,9 @@ METRIC = "track-steps/s"
 # arithmetic as compiled: nothing is recomputed).  They are reported only
 # while the kernel sources are the ones that were measured (SHA-256 below).
 TRAFFIC = {
-    "kernel_sha256": "2c32c17f025de9925db2428ebd6686c3cf76713e3c3c8dd177c5f3bf06e83aa8",
-    "bytes_per_track_step": {"calo/fp64": 102.77, "calo/mixed": 79.31},
-    "fp64_inst_per_track_step": {"calo/fp64": 123.87, "calo/mixed": 28.20},
+    "kernel_sha256": "a4e972fd52d881370801d2272f72c2766265a04d113b0119ccc1404e7916e395",
+    "bytes_per_track_step": {"calo/fp64": 127.66, "calo/mixed": 85.48},
+    "fp64_inst_per_track_step": {"calo/fp64": 110.04, "calo/mixed": 28.20},
     "source": "profiles/step_kernels_calo_dram_traffic.md",
 }
 # FP64 pipe peak: 1.25 TFLOP/s nominal FP64 on GB300 (an FMA counts two
