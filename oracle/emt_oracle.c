@@ -743,8 +743,8 @@ int orc_get_table(const orc_handle* h, int m, int p, int q, double* out)
 
 /* ------------------------------------------------------------------ */
 /* Geometry (a reading of Sec. 3.3: the paper navigates CMS with       */
-/* VecGeom or ORANGE, a CSG of quadric surfaces; this build has two    */
-/* kinds of volumes with exact logical volume indices).                */
+/* VecGeom or ORANGE, a CSG of quadric surfaces; here two simple kinds */
+/* of volumes with exact logical volume indices).                      */
 /* Layers: slabs stacked along +z from z0 inside |x|<=hx, |y|<=hy;     */
 /* volume -1 is the vacuum of the world box; -2 is outside the world.  */
 /* Cylinders: concentric shells about the z axis (Sec. 4's test        */
