@@ -609,15 +609,17 @@ static int find_bin(const orc_handle* h, double E)
 
 /* piecewise linear in E between nodes; constant outside the grid.  The
  * fraction within an interval is (E - E_n) times the interval's reciprocal
- * width, rounded once when the grid is built (a reading: the paper fixes no
- * interpolation arithmetic; a product instead of a quotient per lookup). */
+ * width, rounded once when the grid is built, and v_n + (v_{n+1} - v_n) f
+ * is one fused multiply-add (a reading: the paper fixes no interpolation
+ * arithmetic; a product instead of a quotient per lookup, one rounding
+ * instead of two).  The straight-line move x + s u is fused likewise. */
 static double lookup(const orc_handle* h, const double* v, double E)
 {
     if (E <= h->grid[0]) return v[0];
     if (E >= h->grid[h->n_grid - 1]) return v[h->n_grid - 1];
     int n = find_bin(h, E);
     double f = (E - h->grid[n]) * h->igrid[n];
-    return v[n] + (v[n + 1] - v[n]) * f;
+    return fma(v[n + 1] - v[n], f, v[n]);
 }
 
 /* range: linear through the origin below the first node, linear between
@@ -627,7 +629,7 @@ static double range_of(const orc_handle* h, const double* R, double T)
     if (T < h->grid[0]) return R[0] * (T / h->grid[0]);
     int n = find_bin(h, T);
     double f = (T - h->grid[n]) * h->igrid[n];
-    return R[n] + (R[n + 1] - R[n]) * f;
+    return fma(R[n + 1] - R[n], f, R[n]);
 }
 
 /* inverse of range_of (the same piecewise-linear function, inverted with
@@ -638,7 +640,7 @@ static double inv_range_of(const orc_handle* h, const double* R, const double* i
     int n = 0;
     while (n + 1 < h->n_grid - 1 && R[n + 1] <= r) ++n;
     double f = (r - R[n]) * irs[n];
-    return h->grid[n] + (h->grid[n + 1] - h->grid[n]) * f;
+    return fma(h->grid[n + 1] - h->grid[n], f, h->grid[n]);
 }
 
 static const double* irs_of(const orc_handle* h, int m, int p) { return h->irs + ((size_t)m * 3 + p) * h->n_grid; }
@@ -1359,34 +1361,40 @@ int orc_sample(int process, double E, double cut_e, double cut_g, uint32_t seed,
  * bounds the work of one step of a looping low-energy track). */
 #define MAX_SUBSTEPS 100
 
+/* The RK4 arithmetic is written with fused multiply-adds where a product
+ * is added (one rounding each; a reading: the integrator's rounding is not
+ * fixed by the paper). */
 static void cross(const double a[3], const double b[3], double o[3])
 {
-    o[0] = a[1] * b[2] - a[2] * b[1];
-    o[1] = a[2] * b[0] - a[0] * b[2];
-    o[2] = a[0] * b[1] - a[1] * b[0];
+    o[0] = fma(a[1], b[2], -(a[2] * b[1]));
+    o[1] = fma(a[2], b[0], -(a[0] * b[2]));
+    o[2] = fma(a[0], b[1], -(a[1] * b[0]));
 }
 
 static void rk4(const orc_handle* h, double kq, const double x[3], const double u[3], double hs, double xo[3],
                 double uo[3])
 {
     double a1[3], a2[3], a3[3], a4[3], u2[3], u3[3], u4[3], t[3];
+    double hh = 0.5 * hs;
     cross(u, h->B, t);
     for (int i = 0; i < 3; ++i) a1[i] = kq * t[i];
-    for (int i = 0; i < 3; ++i) u2[i] = u[i] + 0.5 * hs * a1[i];
+    for (int i = 0; i < 3; ++i) u2[i] = fma(hh, a1[i], u[i]);
     cross(u2, h->B, t);
     for (int i = 0; i < 3; ++i) a2[i] = kq * t[i];
-    for (int i = 0; i < 3; ++i) u3[i] = u[i] + 0.5 * hs * a2[i];
+    for (int i = 0; i < 3; ++i) u3[i] = fma(hh, a2[i], u[i]);
     cross(u3, h->B, t);
     for (int i = 0; i < 3; ++i) a3[i] = kq * t[i];
-    for (int i = 0; i < 3; ++i) u4[i] = u[i] + hs * a3[i];
+    for (int i = 0; i < 3; ++i) u4[i] = fma(hs, a3[i], u[i]);
     cross(u4, h->B, t);
     for (int i = 0; i < 3; ++i) a4[i] = kq * t[i];
     double h6 = hs / 6.0;
     for (int i = 0; i < 3; ++i) {
-        xo[i] = x[i] + h6 * (u[i] + 2.0 * u2[i] + 2.0 * u3[i] + u4[i]);
-        uo[i] = u[i] + h6 * (a1[i] + 2.0 * a2[i] + 2.0 * a3[i] + a4[i]);
+        double su = fma(2.0, u3[i], fma(2.0, u2[i], u[i])) + u4[i];
+        double sa = fma(2.0, a3[i], fma(2.0, a2[i], a1[i])) + a4[i];
+        xo[i] = fma(h6, su, x[i]);
+        uo[i] = fma(h6, sa, u[i]);
     }
-    double n = sqrt(uo[0] * uo[0] + uo[1] * uo[1] + uo[2] * uo[2]);
+    double n = sqrt(fma(uo[0], uo[0], fma(uo[1], uo[1], uo[2] * uo[2])));
     for (int i = 0; i < 3; ++i) uo[i] = uo[i] / n;
 }
 
@@ -1591,7 +1599,7 @@ static void step_track(const orc_handle* h, uint64_t event_id, track_t* tr, tall
         } else {
             s = s_phys;
         }
-        for (int a = 0; a < 3; ++a) tr->x[a] = tr->x[a] + s * tr->u[a];
+        for (int a = 0; a < 3; ++a) tr->x[a] = fma(s, tr->u[a], tr->x[a]);
         if (boundary && e.axis >= 0) tr->x[e.axis] = e.plane;
     } else {
         double smax = s_phys;

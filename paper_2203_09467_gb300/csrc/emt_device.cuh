@@ -54,6 +54,10 @@ __device__ __forceinline__ double mlog(double x) { return log(x); }
 __device__ __forceinline__ float mlog(float x) { return logf(x); }
 __device__ __forceinline__ double mexp(double x) { return exp(x); }
 __device__ __forceinline__ float mexp(float x) { return expf(x); }
+// a * b + c with one rounding (the interpolations and the straight move,
+// as in the oracle)
+__device__ __forceinline__ double mfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float mfma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double mexpm1(double x) { return expm1(x); }
 __device__ __forceinline__ float mexpm1(float x) { return expm1f(x); }
 __device__ __forceinline__ double mlog1p(double x) { return log1p(x); }
@@ -412,7 +416,7 @@ __device__ __forceinline__ R xs_value(const Params<R>& p, const R* t, const Look
     if (l.clamp < 0) return t[q];
     if (l.clamp > 0) return t[(p.n_grid - 1) * kNq + q];
     R a = t[l.n * kNq + q], b = t[(l.n + 1) * kNq + q];
-    return a + (b - a) * l.f;
+    return mfma(b - a, l.f, a);
 }
 
 // range: linear through the origin below the grid, linear between nodes,
@@ -425,7 +429,7 @@ __device__ __forceinline__ R range_value(const Params<R>& p, const R* t, R T, co
     R f = l.f;
     if (l.clamp > 0) f = (T - p.grid[n]) * p.igrid[n];
     R a = t[n * kNq + 3], b = t[(n + 1) * kNq + 3];
-    return a + (b - a) * f;
+    return mfma(b - a, f, a);
 }
 
 // inverse of range_value with the range intervals' reciprocal widths irs;
@@ -440,7 +444,7 @@ __device__ __forceinline__ R inv_range(const Params<R>& p, const R* t, const R* 
     int top = p.n_grid - 2;
     while (n < top && le_pos(t[(n + 1) * kNq + 3], r)) ++n;
     R f = (r - t[n * kNq + 3]) * irs[n];
-    return p.grid[n] + (p.grid[n + 1] - p.grid[n]) * f;
+    return mfma(p.grid[n + 1] - p.grid[n], f, p.grid[n]);
 }
 
 // ------------------------------------------------------------------ geometry
@@ -699,33 +703,40 @@ template <typename R>
 __device__ __forceinline__ void rk4(const Params<R>& p, R kq, const double x[3], const R u[3], R hs, double xo[3],
                                     R uo[3])
 {
+    // products added to a sum are fused (one rounding each), as in the oracle
     const R B0 = from_d<R>(p.B[0]), B1 = from_d<R>(p.B[1]), B2 = from_d<R>(p.B[2]);
     R a1[3], a2[3], a3[3], a4[3], u2[3], u3[3], u4[3];
-    a1[0] = kq * (u[1] * B2 - u[2] * B1);
-    a1[1] = kq * (u[2] * B0 - u[0] * B2);
-    a1[2] = kq * (u[0] * B1 - u[1] * B0);
+    const R hh = R(0.5) * hs;
+    a1[0] = kq * mfma(u[1], B2, -(u[2] * B1));
+    a1[1] = kq * mfma(u[2], B0, -(u[0] * B2));
+    a1[2] = kq * mfma(u[0], B1, -(u[1] * B0));
 #pragma unroll
-    for (int i = 0; i < 3; ++i) u2[i] = u[i] + R(0.5) * hs * a1[i];
-    a2[0] = kq * (u2[1] * B2 - u2[2] * B1);
-    a2[1] = kq * (u2[2] * B0 - u2[0] * B2);
-    a2[2] = kq * (u2[0] * B1 - u2[1] * B0);
+    for (int i = 0; i < 3; ++i) u2[i] = mfma(hh, a1[i], u[i]);
+    a2[0] = kq * mfma(u2[1], B2, -(u2[2] * B1));
+    a2[1] = kq * mfma(u2[2], B0, -(u2[0] * B2));
+    a2[2] = kq * mfma(u2[0], B1, -(u2[1] * B0));
 #pragma unroll
-    for (int i = 0; i < 3; ++i) u3[i] = u[i] + R(0.5) * hs * a2[i];
-    a3[0] = kq * (u3[1] * B2 - u3[2] * B1);
-    a3[1] = kq * (u3[2] * B0 - u3[0] * B2);
-    a3[2] = kq * (u3[0] * B1 - u3[1] * B0);
+    for (int i = 0; i < 3; ++i) u3[i] = mfma(hh, a2[i], u[i]);
+    a3[0] = kq * mfma(u3[1], B2, -(u3[2] * B1));
+    a3[1] = kq * mfma(u3[2], B0, -(u3[0] * B2));
+    a3[2] = kq * mfma(u3[0], B1, -(u3[1] * B0));
 #pragma unroll
-    for (int i = 0; i < 3; ++i) u4[i] = u[i] + hs * a3[i];
-    a4[0] = kq * (u4[1] * B2 - u4[2] * B1);
-    a4[1] = kq * (u4[2] * B0 - u4[0] * B2);
-    a4[2] = kq * (u4[0] * B1 - u4[1] * B0);
+    for (int i = 0; i < 3; ++i) u4[i] = mfma(hs, a3[i], u[i]);
+    a4[0] = kq * mfma(u4[1], B2, -(u4[2] * B1));
+    a4[1] = kq * mfma(u4[2], B0, -(u4[0] * B2));
+    a4[2] = kq * mfma(u4[0], B1, -(u4[1] * B0));
     R h6 = hs / R(6);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        xo[i] = x[i] + to_d(h6 * (u[i] + R(2) * u2[i] + R(2) * u3[i] + u4[i]));
-        uo[i] = u[i] + h6 * (a1[i] + R(2) * a2[i] + R(2) * a3[i] + a4[i]);
+        const R su = mfma(R(2), u3[i], mfma(R(2), u2[i], u[i])) + u4[i];
+        const R sa = mfma(R(2), a3[i], mfma(R(2), a2[i], a1[i])) + a4[i];
+        if constexpr (sizeof(R) == 8)
+            xo[i] = fma(h6, su, x[i]);
+        else
+            xo[i] = x[i] + to_d(h6 * su);
+        uo[i] = mfma(h6, sa, u[i]);
     }
-    R n = msqrt(uo[0] * uo[0] + uo[1] * uo[1] + uo[2] * uo[2]);
+    R n = msqrt(mfma(uo[0], uo[0], mfma(uo[1], uo[1], uo[2] * uo[2])));
 #pragma unroll
     for (int i = 0; i < 3; ++i) uo[i] = uo[i] / n;
 }

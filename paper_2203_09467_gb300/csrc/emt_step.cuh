@@ -226,7 +226,7 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
             // full navigation would decide
             double x1[3];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) x1[a] = t.x[a] + s_physd * ud[a];
+            for (int a = 0; a < 3; ++a) x1[a] = fma(s_physd, ud[a], t.x[a]);
             if (!chord_inside<G>(p, t.vol, t.x, x1)) {
                 e = nav_exit<G>(p, t.vol, t.x, ud);
                 boundary = e.t <= s_physd;
@@ -234,7 +234,7 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
             if (boundary) {
                 s = e.t;
 #pragma unroll
-                for (int a = 0; a < 3; ++a) t.x[a] = t.x[a] + s * ud[a];
+                for (int a = 0; a < 3; ++a) t.x[a] = fma(s, ud[a], t.x[a]);
                 if (e.axis >= 0) t.x[e.axis] = e.plane;
             } else {
                 s = s_physd;
@@ -252,7 +252,7 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
                 s = s_physd;
             }
 #pragma unroll
-            for (int a = 0; a < 3; ++a) t.x[a] = t.x[a] + s * ud[a];
+            for (int a = 0; a < 3; ++a) t.x[a] = fma(s, ud[a], t.x[a]);
             if (boundary && e.axis >= 0) t.x[e.axis] = e.plane;
         }
     } else {
