@@ -78,9 +78,11 @@ def autotune(name, setup, prim, ids, precision="fp64", use_cache=True, repeats=2
         if ms < best_ms:
             best, best_ms = cfg, ms
     cache[key] = {"best": best, "timings": timings}
-    try:
-        with open(CACHE, "w") as f:
+    try:  # atomic replace: ranks of a multi-GPU run may write at once
+        tmp = f"{CACHE}.{os.getpid()}.tmp"
+        with open(tmp, "w") as f:
             json.dump(cache, f, indent=1)
+        os.replace(tmp, CACHE)
     except OSError:
         pass
     return best, timings
