@@ -47,9 +47,9 @@ METRIC = "track-steps/s"
 # arithmetic as compiled: nothing is recomputed).  They are reported only
 # while the kernel sources are the ones that were measured (SHA-256 below).
 TRAFFIC = {
-    "kernel_sha256": "a4e972fd52d881370801d2272f72c2766265a04d113b0119ccc1404e7916e395",
-    "bytes_per_track_step": {"calo/fp64": 127.66, "calo/mixed": 85.48},
-    "fp64_inst_per_track_step": {"calo/fp64": 110.04, "calo/mixed": 28.20},
+    "kernel_sha256": "a6a3445e2dba55e2220686011f087aa213dc5d4592c65b491dbc7295456c1316",
+    "bytes_per_track_step": {"calo/fp64": 127.91, "calo/mixed": 85.52},
+    "fp64_inst_per_track_step": {"calo/fp64": 103.53, "calo/mixed": 28.20},
     "source": "profiles/step_kernels_calo_dram_traffic.md",
 }
 # FP64 pipe peak: 1.25 TFLOP/s nominal FP64 on GB300 (an FMA counts two

@@ -193,3 +193,26 @@ def test_cms_mixed_statistical(emt, oracle_mod):
         m_gpu = (sh[k] * steps).sum() / sh[k].sum()
         m_orc = (osh[k] * steps).sum() / osh[k].sum()
         assert abs(m_gpu / m_orc - 1) < 0.03, (k, m_gpu, m_orc)
+
+
+def test_cylinder_edge_cases(emt, oracle_mod):
+    """Primaries outside the envelope (beyond r = 375 cm, beyond the end
+    planes), below the cut, on the axis moving along z (no radial surface
+    ahead), exactly on a shell radius and on an end plane, in the vacuum
+    core and in every material; compared event by event with the oracle."""
+    s = W.cms_setup()
+    R = W.CMS_RADII
+    pos = [[0, 0, 0], [400.0, 0, 0], [0, 0, 701.0], [50.0, 0, 10.0], [0, 0, -3.0], [R[0], 0, 0],
+           [0, -R[2], 20.0], [10.0, 0, 700.0], [200.0, 0, -650.0], [340.0, 10.0, 0]]
+    dirs = [[1, 0, 0], [1, 0, 0], [0, 0, 1], [0, 0, 1], [0, 0, -1], [1, 0, 0], [0, 1, 0], [0, 0, 1],
+            [0.6, 0, -0.8], [-1, 0, 0]]
+    types = [0, 1, 0, 2, 0, 1, 2, 0, 1, 0]
+    T = [1000.0, 500.0, 300.0, 0.6, 2000.0, 800.0, 3000.0, 50.0, 400.0, 700.0]
+    n = len(pos)
+    prim = {"event": np.arange(n, dtype=np.int32), "type": np.array(types, np.int32), "T": np.array(T),
+            "pos": np.array(pos, float), "dir": np.array(dirs, float)}
+    hist, summ, st, _ = gpu_run(emt, s, prim, n)
+    ohist, osumm = oracle_of(oracle_mod, s).run(prim, n, np.arange(n))
+    assert summ[1, 1] == 500.0 and summ[2, 1] == 300.0   # outside the world: escaped
+    assert summ[3, 0] == 0.6 + 2 * 0.51099895 or abs(summ[3, 0] - (0.6 + 2 * 0.51099895)) < 1e-12
+    check_events(summ, osumm, hist, ohist)
