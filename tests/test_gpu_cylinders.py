@@ -216,3 +216,25 @@ def test_cylinder_edge_cases(emt, oracle_mod):
     assert summ[1, 1] == 500.0 and summ[2, 1] == 300.0   # outside the world: escaped
     assert summ[3, 0] == 0.6 + 2 * 0.51099895 or abs(summ[3, 0] - (0.6 + 2 * 0.51099895)) < 1e-12
     check_events(summ, osumm, hist, ohist)
+
+
+def test_invalid_geometry_and_options_rejected(emt):
+    """Cylinders need z0 = 0 and a positive half-length; scoring along z needs
+    a non-empty range; track selection needs the split schedule, the host
+    spill low-energy selection with a budget at least max_active."""
+    s = W.cms_setup()
+    ctx = emt.Context(slot_capacity=1 << 12, max_events=4, max_bins=200)
+    ctx.load_materials(s.materials, s.physics)
+    for k, v in [(0, 5.0), (17, 0.0), (20, -700.0)]:  # z0, half_z, score range
+        w = s.world.copy()
+        w[k] = v
+        with pytest.raises(emt.EmtError) as e:
+            ctx.load_geometry(s.layers, w)
+        assert e.value.status == -1
+    ctx.load_geometry(s.layers, s.world)
+    ctx.close()
+    for kw in [dict(max_active=100, schedule="fused"),
+               dict(max_active=100, schedule="split", select="order", spill_above=200),
+               dict(max_active=100, schedule="split", select="low_energy", spill_above=50)]:
+        with pytest.raises(emt.EmtError):
+            emt.Context(slot_capacity=1 << 12, max_events=4, **kw)
