@@ -40,6 +40,7 @@ struct Plan {
     size_t cnt, status, total_steps, done_head, ehist;
     size_t hist, ledger, counts, live, event_id, done_ring;
     size_t grid, gridf, igrid, igridf, irs, irsf, tab, tabf, dedx, mats, bk, vacuum, x0, ray_a, scratch;
+    size_t dgrid, dgridf, dtab, dtabf;
     size_t zb, lmat, lbin;
     size_t st_ev, st_type, st_T, st_pos, st_dir, st_uid, st_slot, st_ids, st_start, st_runs;
     size_t slots_tmp, out_hist, out_summary;
@@ -88,6 +89,10 @@ Plan make_plan(const emt_options& o)
     p.irsf = p.add((size_t)kMaxMat * 3 * kMaxGrid * sizeof(float));
     p.tab = p.add((size_t)kMaxMat * 3 * kMaxGrid * kNq * sizeof(double));
     p.tabf = p.add((size_t)kMaxMat * 3 * kMaxGrid * kNq * sizeof(float));
+    p.dgrid = p.add(kMaxGrid * sizeof(double));
+    p.dgridf = p.add(kMaxGrid * sizeof(float));
+    p.dtab = p.add((size_t)kMaxMat * 3 * kMaxGrid * kNq * sizeof(double));
+    p.dtabf = p.add((size_t)kMaxMat * 3 * kMaxGrid * kNq * sizeof(float));
     p.dedx = p.add((size_t)kMaxMat * 3 * kMaxGrid * sizeof(double));
     p.mats = p.add(kMaxMat * sizeof(MaterialDev));
     p.bk = p.add(kMaxMat * sizeof(double));
@@ -884,6 +889,10 @@ emt_status emt_load_materials(emt_ctx* c, const emt_material* mats, int32_t n, c
     b.irs = c->at<double>(pl.irs);
     b.igridf = c->mixed() ? c->at<float>(pl.igridf) : nullptr;
     b.irsf = c->mixed() ? c->at<float>(pl.irsf) : nullptr;
+    b.dgrid = c->at<double>(pl.dgrid);
+    b.dtab = c->at<double>(pl.dtab);
+    b.dgridf = c->mixed() ? c->at<float>(pl.dgridf) : nullptr;
+    b.dtabf = c->mixed() ? c->at<float>(pl.dtabf) : nullptr;
     EMT_CUDA(c, build_tables(b, c->at<double>(pl.scratch), c->stream));
     EMT_CUDA(c, cudaStreamSynchronize(c->stream));
     c->n_mat = n;
@@ -902,6 +911,10 @@ emt_status emt_load_materials(emt_ctx* c, const emt_material* mats, int32_t n, c
     c->pd.irs = b.irs;
     c->pf.igrid = c->at<float>(pl.igridf);
     c->pf.irs = c->at<float>(pl.irsf);
+    c->pd.dgrid = b.dgrid;
+    c->pd.dtab = b.dtab;
+    c->pf.dgrid = c->at<float>(pl.dgridf);
+    c->pf.dtab = c->at<float>(pl.dtabf);
     c->pd.n_grid = c->pf.n_grid = n_grid;
     c->pd.bpd = c->pf.bpd = ph->bins_per_decade;
     c->pd.log10_lo = c->pf.log10_lo = l10;
@@ -1412,6 +1425,10 @@ extern "C" emt_status emt_transport_static(int32_t device, uint32_t seed, const 
     b.irs = reinterpret_cast<double*>(pool + pl.irs);
     b.igridf = nullptr;
     b.irsf = nullptr;
+    b.dgrid = reinterpret_cast<double*>(pool + pl.dgrid);
+    b.dtab = reinterpret_cast<double*>(pool + pl.dtab);
+    b.dgridf = nullptr;
+    b.dtabf = nullptr;
     if (build_tables(b, reinterpret_cast<double*>(pool + pl.scratch), st) != cudaSuccess) return EMT_ERR_CUDA;
     for (int k = 0; k < 3; ++k) {
         p.cut[k] = ph->cut_MeV[k];
@@ -1421,6 +1438,8 @@ extern "C" emt_status emt_transport_static(int32_t device, uint32_t seed, const 
     p.tab = b.tab;
     p.igrid = b.igrid;
     p.irs = b.irs;
+    p.dgrid = b.dgrid;
+    p.dtab = b.dtab;
     p.n_grid = n_grid;
     p.bpd = ph->bins_per_decade;
     p.log10_lo = (float)std::log10(ph->grid_lo_MeV);

@@ -156,6 +156,8 @@ struct Params {
     const R* tab;
     const R* igrid;  // 1 / (grid[n+1] - grid[n])
     const R* irs;    // [(m * 3 + p) * n_grid + n]: 1 / (R[n+1] - R[n]) of the range tables
+    const R* dgrid;  // grid[n+1] - grid[n]
+    const R* dtab;   // layout of tab: tab[n+1][q] - tab[n][q]
     int n_grid;
     int bpd;
     float log10_lo;  // log10(grid[0]) for the bin guess
@@ -362,9 +364,20 @@ __device__ __forceinline__ uint64_t child_uid(uint32_t seed, uint64_t event_id, 
 }
 
 // ------------------------------------------------------------------ tables
-// positive IEEE doubles (and floats) order like their bit patterns
+// Comparisons on the integer pipe (the FP64 pipe is narrow).  The signed
+// order of the bit patterns of two IEEE values is their numeric order when
+// neither is NaN and at least one of them is > 0: two non-negative values
+// order like their bits, and a negative value or -0 has a negative pattern,
+// below every positive one.  Every call site has one operand > 0 (a grid
+// node, a cut, a step limit, a range, a cross-section sum).
 __device__ __forceinline__ bool le_pos(double a, double b) { return __double_as_longlong(a) <= __double_as_longlong(b); }
 __device__ __forceinline__ bool le_pos(float a, float b) { return __float_as_int(a) <= __float_as_int(b); }
+__device__ __forceinline__ bool lt_pos(double a, double b) { return __double_as_longlong(a) < __double_as_longlong(b); }
+__device__ __forceinline__ bool lt_pos(float a, float b) { return a < b; }
+// a > 0 and a != 0, exact for every value (NaN: false and true)
+__device__ __forceinline__ bool gt_zero(double a) { return __double_as_longlong(a) > 0; }
+__device__ __forceinline__ bool gt_zero(float a) { return a > 0.0f; }
+__device__ __forceinline__ bool nonzero(double a) { return ((unsigned long long)__double_as_longlong(a) << 1) != 0ull; }
 
 // node n with grid[n] <= E < grid[n+1], clamped to [0, n_grid-2]: an FP32
 // logarithm guesses, exact comparisons with the nodes decide.
@@ -393,13 +406,13 @@ __device__ __forceinline__ Lookup<R> locate_energy(const Params<R>& p, R E)
 {
     Lookup<R> l;
     l.clamp = 0;
-    if (E <= p.grid[0]) {
+    if (le_pos(E, p.grid[0])) {
         l.clamp = -1;
         l.n = 0;
         l.f = R(0);
         return l;
     }
-    if (E >= p.grid[p.n_grid - 1]) {
+    if (le_pos(p.grid[p.n_grid - 1], E)) {
         l.clamp = 1;
         l.n = p.n_grid - 2;
         l.f = R(0);
@@ -410,26 +423,25 @@ __device__ __forceinline__ Lookup<R> locate_energy(const Params<R>& p, R E)
     return l;
 }
 
+// t, dt: the rows of tab and dtab of one material and particle type
 template <typename R>
-__device__ __forceinline__ R xs_value(const Params<R>& p, const R* t, const Lookup<R>& l, int q)
+__device__ __forceinline__ R xs_value(const Params<R>& p, const R* t, const R* dt, const Lookup<R>& l, int q)
 {
     if (l.clamp < 0) return t[q];
     if (l.clamp > 0) return t[(p.n_grid - 1) * kNq + q];
-    R a = t[l.n * kNq + q], b = t[(l.n + 1) * kNq + q];
-    return mfma(b - a, l.f, a);
+    return mfma(dt[l.n * kNq + q], l.f, t[l.n * kNq + q]);
 }
 
 // range: linear through the origin below the grid, linear between nodes,
 // extrapolated with the last slope above
 template <typename R>
-__device__ __forceinline__ R range_value(const Params<R>& p, const R* t, R T, const Lookup<R>& l)
+__device__ __forceinline__ R range_value(const Params<R>& p, const R* t, const R* dt, R T, const Lookup<R>& l)
 {
-    if (T < p.grid[0]) return t[3] * (T / p.grid[0]);
+    if (lt_pos(T, p.grid[0])) return t[3] * (T / p.grid[0]);
     int n = l.n;
     R f = l.f;
     if (l.clamp > 0) f = (T - p.grid[n]) * p.igrid[n];
-    R a = t[n * kNq + 3], b = t[(n + 1) * kNq + 3];
-    return mfma(b - a, f, a);
+    return mfma(dt[n * kNq + 3], f, t[n * kNq + 3]);
 }
 
 // inverse of range_value with the range intervals' reciprocal widths irs;
@@ -438,13 +450,13 @@ __device__ __forceinline__ R range_value(const Params<R>& p, const R* t, R T, co
 template <typename R>
 __device__ __forceinline__ R inv_range(const Params<R>& p, const R* t, const R* irs, R r, int nstart)
 {
-    if (r < t[3]) return p.grid[0] * (r / t[3]);
+    if (lt_pos(r, t[3])) return p.grid[0] * (r / t[3]);
     int n = nstart;
     while (n > 0 && !le_pos(t[n * kNq + 3], r)) --n;
     int top = p.n_grid - 2;
     while (n < top && le_pos(t[(n + 1) * kNq + 3], r)) ++n;
     R f = (r - t[n * kNq + 3]) * irs[n];
-    return mfma(p.grid[n + 1] - p.grid[n], f, p.grid[n]);
+    return mfma(p.dgrid[n], f, p.grid[n]);
 }
 
 // ------------------------------------------------------------------ geometry
@@ -598,19 +610,19 @@ __device__ __forceinline__ Exit nav_exit_layers(const Params<R>& p, int vol, con
         int nx[3];
         bool has[3];
         float tf[3];
-        has[2] = d[2] != 0.0;
-        if (d[2] > 0.0) {
+        has[2] = nonzero(d[2]);
+        if (gt_zero(d[2])) {
             pl[2] = p.zb[vol + 1];
             nx[2] = vol + 1 < L ? vol + 1 : kVolWorld;
         } else {
             pl[2] = p.zb[vol];
             nx[2] = vol > 0 ? vol - 1 : kVolWorld;
         }
-        has[0] = d[0] != 0.0;
-        pl[0] = d[0] > 0.0 ? p.hx : -p.hx;
+        has[0] = nonzero(d[0]);
+        pl[0] = gt_zero(d[0]) ? p.hx : -p.hx;
         nx[0] = kVolWorld;
-        has[1] = d[1] != 0.0;
-        pl[1] = d[1] > 0.0 ? p.hy : -p.hy;
+        has[1] = nonzero(d[1]);
+        pl[1] = gt_zero(d[1]) ? p.hy : -p.hy;
         nx[1] = kVolWorld;
         float tmin = __int_as_float(0x7F800000);
 #pragma unroll

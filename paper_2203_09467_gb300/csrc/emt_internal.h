@@ -31,6 +31,10 @@ struct TableBuild {
     double* irs;    // [n_mat][3][n_grid] 1 / (R[n+1] - R[n]) of the range tables
     float* igridf;  // optional float copies
     float* irsf;
+    double* dgrid;  // [n_grid] grid[n+1] - grid[n] (last entry 0)
+    double* dtab;   // [n_mat][3][n_grid][4] tab[n+1][q] - tab[n][q] (last node 0)
+    float* dgridf;  // optional: the same differences of the float copies, in float
+    float* dtabf;
 };
 
 // scratch: (32 + n_mat * 2 * n_grid) doubles

@@ -89,7 +89,7 @@ enum Model : int {
 template <typename R>
 __device__ __forceinline__ void deposit_now(const Params<R>& p, uint32_t ev, int col, double e)
 {
-    if (e == 0.0) return;
+    if (!nonzero(e)) return;
     atomicAdd(&p.hist[(size_t)ev * p.hstride + col], e);
 }
 
@@ -127,8 +127,8 @@ __device__ __forceinline__ void apply_effects(const Params<R>& p, uint32_t ev, i
                                               const Effects& fx)
 {
     deposit_now(p, ev, fx.col, fx.dep);
-    if (fx.esc != 0.0) atomicAdd(&p.ledger[3 * (size_t)ev + 0], fx.esc);
-    if (fx.kill != 0.0) atomicAdd(&p.ledger[3 * (size_t)ev + 1], fx.kill);
+    if (nonzero(fx.esc)) atomicAdd(&p.ledger[3 * (size_t)ev + 0], fx.esc);
+    if (nonzero(fx.kill)) atomicAdd(&p.ledger[3 * (size_t)ev + 1], fx.kill);
     if (fx.finished) finish_track(p, ev, type, steps);
     update_live(p, ev, fx.live_delta);
 }
@@ -165,7 +165,9 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
     // photons: photo, Compton, pair (+ Rayleigh); e-: ioni, brems; e+: ioni,
     // brems, annihilation
     const int nproc = t.type == 1 ? 2 : ((X && t.type == 0 && (p.mask & kProcRayleigh)) ? 4 : 3);
-    const R* tab = matter ? p.tab + (size_t)(mi * 3 + t.type) * p.n_grid * kNq : nullptr;
+    const size_t row = matter ? (size_t)(mi * 3 + t.type) * p.n_grid * kNq : 0;
+    const R* tab = p.tab + row;
+    const R* dtab = p.dtab + row;
 
     R sig[4] = {R(0), R(0), R(0), R(0)};
     R sig_tot = R(0);
@@ -176,37 +178,37 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
     lk.clamp = -1;
     if (matter) {
         lk = locate_energy(p, t.T);
-        sig[0] = xs_value(p, tab, lk, 0);
-        sig[1] = xs_value(p, tab, lk, 1);
+        sig[0] = xs_value(p, tab, dtab, lk, 0);
+        sig[1] = xs_value(p, tab, dtab, lk, 1);
         sig_tot = sig[0] + sig[1];
         if (nproc >= 3) {
-            sig[2] = xs_value(p, tab, lk, 2);
+            sig[2] = xs_value(p, tab, dtab, lk, 2);
             sig_tot = sig_tot + sig[2];
         }
         if constexpr (X) {
             if (nproc == 4) {
-                sig[3] = xs_value(p, tab, lk, 3);
+                sig[3] = xs_value(p, tab, dtab, lk, 3);
                 sig_tot = sig_tot + sig[3];
             }
         }
     }
     const R kInf = R(__longlong_as_double(0x7FF0000000000000ll));
     R s_int = kInf;
-    if (sig_tot > R(0)) {
+    if (gt_zero(sig_tot)) {
         dr.next = 0;
         s_int = -mlog(draw<R>(dr)) / sig_tot;
     }
     R s_max = kInf;
     if (charged && matter) {
-        Rng = range_value(p, tab, t.T, lk);
+        Rng = range_value(p, tab, dtab, t.T, lk);
         R fr_lim = pfinal_range(p);
-        R lim = Rng < fr_lim ? Rng : fr_lim;
+        R lim = lt_pos(Rng, fr_lim) ? Rng : fr_lim;
         R fr = pstep_frac(p) * Rng;
-        s_max = fr > lim ? fr : lim;
+        s_max = lt_pos(lim, fr) ? fr : lim;
     }
     R s_phys = s_max;
     bool interact = false;
-    if (s_int < s_max) {
+    if (lt_pos(s_int, s_max)) {
         s_phys = s_int;
         interact = true;
     }
@@ -229,7 +231,7 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
             for (int a = 0; a < 3; ++a) x1[a] = fma(s_physd, ud[a], t.x[a]);
             if (!chord_inside<G>(p, t.vol, t.x, x1)) {
                 e = nav_exit<G>(p, t.vol, t.x, ud);
-                boundary = e.t <= s_physd;
+                boundary = le_pos(e.t, s_physd);
             }
             if (boundary) {
                 s = e.t;
@@ -245,7 +247,7 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
             // thin layers: most steps cross a plane; the navigation (with
             // its FP32 prefilter) is cheaper than a test that mostly fails
             e = nav_exit<G>(p, t.vol, t.x, ud);
-            if (e.t <= s_physd) {
+            if (le_pos(e.t, s_physd)) {
                 s = e.t;
                 boundary = true;
             } else {
@@ -282,18 +284,18 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
     // 6-7: continuous loss
     if (charged && matter) {
         R r = Rng - from_d<R>(s);
-        R Tn = r > R(0) ? inv_range(p, tab, p.irs + (size_t)(mi * 3 + t.type) * p.n_grid, r, lk.n) : R(0);
+        R Tn = gt_zero(r) ? inv_range(p, tab, p.irs + (size_t)(mi * 3 + t.type) * p.n_grid, r, lk.n) : R(0);
         R ed = t.T - Tn;
-        fx.dep += to_d(ed);
+        fx.dep = to_d(ed);  // 0 + ed: ed is never -0
         t.T = Tn;
-        if (t.T < pcut(p, t.type)) {
+        if (lt_pos(t.T, pcut(p, t.type))) {
             fx.dep += to_d(t.T) + rest_energy(t.type);
             alive = false;
         }
     }
     // 6b: multiple scattering at the post-step point (boundary steps too)
     if constexpr (X) {
-        if (alive && charged && matter && (p.mask & kProcMsc) && s > 0.0)
+        if (alive && charged && matter && (p.mask & kProcMsc) && gt_zero(s))
             msc_deflect(dr, T0, from_d<R>(s), from_d<R>(p.x0[mi]), t.u);
     }
     // 8: boundary
@@ -313,7 +315,7 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
     R c = R(0);
     for (int i = 0; i < nproc; ++i) {
         c += sig[i];
-        if (xsel < c) {
+        if (lt_pos(xsel, c)) {
             proc = i;
             break;
         }
@@ -397,7 +399,7 @@ __device__ __forceinline__ void interaction_part(const Params<R>& p, TrackReg<R>
     for (int k = 0; k < pr.n; ++k) {
         int st = pr.type[k];
         R sT = pr.T[k];
-        if (sT < pcut(p, st)) {
+        if (lt_pos(sT, pcut(p, st))) {
             fx.dep += to_d(sT) + rest_energy(st);
             continue;
         }
@@ -412,7 +414,7 @@ __device__ __forceinline__ void interaction_part(const Params<R>& p, TrackReg<R>
     bool alive = true;
     if (!pr.parent_alive) {
         alive = false;
-    } else if (t.T < pcut(p, t.type)) {
+    } else if (lt_pos(t.T, pcut(p, t.type))) {
         fx.dep += to_d(t.T) + rest_energy(t.type);
         alive = false;
     }

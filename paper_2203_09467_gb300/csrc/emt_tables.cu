@@ -333,6 +333,18 @@ __global__ void k_to_float(const double* src, float* dst, int n)
     if (i < n) dst[i] = (float)src[i];
 }
 
+// differences of consecutive nodes, v[(row * n + i) * q + j]: d = v[i+1] - v[i]
+// (0 at the last node); the interpolations use them as b - a, the same
+// value the subtraction gives at lookup time
+template <typename T>
+__global__ void k_node_diff(const T* v, T* d, int total, int n, int q)
+{
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int i = (idx / q) % n;
+    d[idx] = i + 1 < n ? v[idx + q] - v[idx] : T(0);
+}
+
 }  // namespace
 
 // reciprocal interval widths of the energy grid and of the range tables
@@ -378,12 +390,16 @@ cudaError_t build_tables(const TableBuild& b, double* scratch, cudaStream_t st)
     k_range_scan<<<1, 64, 0, st>>>(b, acc);
     const int nr = b.n_mat * 3 * b.n_grid;
     k_reciprocals<<<(nr + 127) / 128, 128, 0, st>>>(b);
+    const int nt = b.n_mat * 3 * b.n_grid * kNq;
+    k_node_diff<<<(nt + 255) / 256, 256, 0, st>>>(b.tab, b.dtab, nt, b.n_grid, kNq);
+    k_node_diff<<<(b.n_grid + 255) / 256, 256, 0, st>>>(b.grid, b.dgrid, b.n_grid, b.n_grid, 1);
     if (b.tabf) {
-        int nt = b.n_mat * 3 * b.n_grid * kNq;
         k_to_float<<<(nt + 255) / 256, 256, 0, st>>>(b.tab, b.tabf, nt);
         k_to_float<<<(b.n_grid + 255) / 256, 256, 0, st>>>(b.grid, b.gridf, b.n_grid);
         k_to_float<<<(b.n_grid + 255) / 256, 256, 0, st>>>(b.igrid, b.igridf, b.n_grid);
         k_to_float<<<(nr + 255) / 256, 256, 0, st>>>(b.irs, b.irsf, nr);
+        k_node_diff<<<(nt + 255) / 256, 256, 0, st>>>(b.tabf, b.dtabf, nt, b.n_grid, kNq);
+        k_node_diff<<<(b.n_grid + 255) / 256, 256, 0, st>>>(b.gridf, b.dgridf, b.n_grid, b.n_grid, 1);
     }
     return cudaGetLastError();
 }
