@@ -47,9 +47,9 @@ METRIC = "track-steps/s"
 # arithmetic as compiled: nothing is recomputed).  They are reported only
 # while the kernel sources are the ones that were measured (SHA-256 below).
 TRAFFIC = {
-    "kernel_sha256": "a6a3445e2dba55e2220686011f087aa213dc5d4592c65b491dbc7295456c1316",
-    "bytes_per_track_step": {"calo/fp64": 127.91, "calo/mixed": 85.52},
-    "fp64_inst_per_track_step": {"calo/fp64": 103.53, "calo/mixed": 28.20},
+    "kernel_sha256": "c46928af7038add72deb3317136261db115ed2e5864818097fee0ac0a36750b3",
+    "bytes_per_track_step": {"calo/fp64": 128.20, "calo/mixed": 85.18},
+    "fp64_inst_per_track_step": {"calo/fp64": 86.87, "calo/mixed": 25.82},
     "source": "profiles/step_kernels_calo_dram_traffic.md",
 }
 # FP64 pipe peak: 1.25 TFLOP/s nominal FP64 on GB300 (an FMA counts two
