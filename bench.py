@@ -131,6 +131,11 @@ class ClockSampler:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=self.out, stderr=subprocess.DEVNULL)
+            # nvidia-smi takes a moment to start: wait (at most 3 s) for its
+            # first sample so that the samples cover the timed region
+            t0 = time.monotonic()
+            while os.path.getsize(self.path) == 0 and time.monotonic() - t0 < 3.0 and self.proc.poll() is None:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
 
