@@ -87,7 +87,9 @@ def test_continuous_slowing_down_follows_range(oracle_mod):
         t, sec, info = o.step_one(t, 1, 0)
         path += info[0]
         edep += info[1]
-        assert info[0] <= max(0.2 * Rb, min(Rb, 0.1)) * (1 + 1e-12)
+        # no discrete process and no boundary: every step is the e+- step
+        # limit max(f R, min(R, r_final)) itself
+        assert info[0] == pytest.approx(max(0.2 * Rb, min(Rb, 0.1)), rel=1e-12, abs=0)
         if info[5] == 0:
             break
     assert info[5] == 0
@@ -221,3 +223,54 @@ def test_shower_maximum_is_plausible(oracle_mod):
     tmax = (np.argmax(pair) + 0.5) * x0_pair
     assert 3.0 < tmax < 9.0
     assert 0.95 < summ[:, 0].mean() / 1e4 <= 1.0
+
+
+@pytest.mark.parametrize("ptype,mask,node", [(0, 7, 40), (0, 7, 32), (1, 24, 40), (2, 56, 40), (2, 56, 28)])
+def test_process_selection_frequencies(oracle_mod, ptype, mask, node):
+    """The model of an interaction is chosen with probability Sigma_i /
+    Sigma_tot (competing processes, Sec. 3.2): at a grid node the
+    interpolated Sigma's are the table entries, so the counts over many
+    independent draw streams are multinomial with those probabilities."""
+    s = W.slab_setup(mask=mask, thickness=1e4)
+    s.world[3:9] = [-1e5, -1e5, -1e5, 1e5, 1e5, 1e5]
+    s.world[1] = s.world[2] = 1e4
+    o = make(oracle_mod, s)
+    T = o.grid()[node]
+    nq = 3 if ptype != 1 else 2
+    sig = np.array([o.table(0, ptype, q)[node] for q in range(nq)])
+    pid_of = {0: [oracle_mod.PHOTO, oracle_mod.COMPTON, oracle_mod.PAIR],
+              1: [oracle_mod.IONI, oracle_mod.BREMS],
+              2: [oracle_mod.IONI, oracle_mod.BREMS, oracle_mod.ANNIH]}[ptype]
+    counts = np.zeros(nq)
+    n = 0
+    for uid in range(1, 40001):
+        t = np.array([ptype, T, 0, 0, 5e3, 0, 0, 1, 0, 0], float)
+        t, sec, info = o.step_one(t, uid, 5)
+        if info[3] != 1:
+            continue  # an e+- step ended by its step limit
+        counts[pid_of.index(int(info[4]))] += 1
+        n += 1
+    assert n > 5000
+    expected = n * sig / sig.sum()
+    keep = expected > 5
+    assert stats.chisquare(counts[keep], expected[keep] * counts[keep].sum() / expected[keep].sum()).pvalue > 1e-3
+    assert counts[~keep].sum() <= 3 * max(expected[~keep].sum(), 1.0)
+
+
+def test_step_count_limit_kills_the_track(oracle_mod):
+    """At the step limit the track ends and its energy (+ 2 m for e+) is
+    tallied as killed; the ledger still closes."""
+    for ptype, rest in [(1, 0.0), (2, 2 * ME)]:
+        s = W.slab_setup(mask=0, thickness=100.0)
+        s.world[1] = s.world[2] = 100.0
+        s.world[13] = 3
+        o = make(oracle_mod, s)
+        T0 = 500.0
+        t = np.array([ptype, T0, 0, 0, 1.0, 0, 0, 1, 0, 0], float)
+        for _ in range(3):
+            t, sec, info = o.step_one(t, 1, 0)
+        assert info[5] == 0 and info[7] == pytest.approx(t[1] + rest, rel=1e-15)
+        hist, summ = o.run(one_primary(ptype, T0, [0, 0, 1.0], [0, 0, 1]), 1, [0])
+        assert summ[0, 4] == 3 and summ[0, 5] == 1
+        assert summ[0, 2] == pytest.approx(t[1] + rest, rel=1e-12)
+        assert summ[0, 0] + summ[0, 2] == pytest.approx(T0 + rest, rel=1e-12)
