@@ -274,3 +274,29 @@ def test_step_count_limit_kills_the_track(oracle_mod):
         assert summ[0, 4] == 3 and summ[0, 5] == 1
         assert summ[0, 2] == pytest.approx(t[1] + rest, rel=1e-12)
         assert summ[0, 0] + summ[0, 2] == pytest.approx(T0 + rest, rel=1e-12)
+
+
+def test_deposits_are_scored_in_the_volume_traversed(oracle_mod):
+    """A step's continuous loss is scored in the bin of the volume the step
+    was taken in (the pre-step volume), also when the step ends on a plane:
+    the histogram of a full run equals the per-step deposits binned by the
+    pre-step layer."""
+    s = W.calo_setup(mask=0)
+    o = make(oracle_mod, s)
+    T0 = 300.0
+    t = np.array([1, T0, 0.1, 0.2, -1.0, 0, 0, 1, -1, 0], float)
+    expected = np.zeros(o.n_bins)
+    crossings = 0
+    for _ in range(100000):
+        vol = int(t[8])
+        t, sec, info = o.step_one(t, 1, 0)
+        if info[1] != 0.0:
+            assert vol >= 0
+            expected[int(s.layers[vol, 2])] += info[1]
+        crossings += int(info[2])
+        if info[5] == 0:
+            break
+    assert info[5] == 0 and crossings > 10
+    hist, summ = o.run(one_primary(1, T0, [0.1, 0.2, -1.0], [0, 0, 1]), 1, [0])
+    assert np.count_nonzero(expected) > 10
+    np.testing.assert_allclose(hist[0, : o.n_bins], expected, rtol=1e-12, atol=0)
