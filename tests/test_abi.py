@@ -54,3 +54,29 @@ def test_pool_size_and_options_without_gpu():
     assert n2 - n3 >= 2 * 16 * (1 << 23)
     o.block_size = 96
     assert L.emt_pool_bytes(ctypes.byref(o)) == 0  # invalid options
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No fallback: without the CUDA library the binding raises."""
+    import pytest
+    from paper_2203_09467_gb300 import build, emt
+    monkeypatch.setattr(emt, "_lib", None)
+    monkeypatch.setattr(build, "LIB", str(tmp_path / "absent.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        emt.lib(build_if_missing=False)
+
+
+def test_create_without_a_gpu_returns_the_cuda_status():
+    """Without a usable GPU emt_create reports EMT_ERR_CUDA and hands out no
+    context (nothing runs on the host instead)."""
+    import pytest
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2203_09467_gb300 import emt
+    L = emt.lib()
+    o = emt.Options()
+    L.emt_default_options(ctypes.byref(o))
+    h = ctypes.c_void_p()
+    assert L.emt_create(ctypes.byref(o), ctypes.byref(h)) == -3
+    assert h.value is None
