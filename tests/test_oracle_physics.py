@@ -155,6 +155,25 @@ def test_unrestricted_collision_loss_is_plausible(L):
     assert 0.8 < s.min() < 1.3
 
 
+@pytest.mark.parametrize("Z,A,rho,I", [(82, 207.2, 11.35, 823.0), (18, 39.948, 1.396, 188.0)])
+@pytest.mark.parametrize("charge", [-1, 1])
+def test_restricted_loss_reaches_the_fermi_plateau(L, Z, A, rho, I, charge):
+    """With the high-energy density-effect asymptote, delta = 2 ln(beta
+    gamma) + 2 ln(hbar omega_p / I) - 1, the restricted collision loss tends
+    to the Fermi plateau 2 pi r_e^2 m n_el ln(2 cut m / (hbar omega_p)^2) as
+    T grows with the cut fixed (the tau-dependence of the logarithm, of
+    F+-(tau, Delta) and of delta cancel; the constant terms cancel for both
+    charges), with hbar omega_p = 28.816 sqrt(rho Z / A) eV."""
+    cut = 1.0
+    nel = rho * NA / A * Z
+    hwp = 28.816e-6 * np.sqrt(rho * Z / A)
+    plateau = 2 * np.pi * RE**2 * ME * nel * np.log(2 * cut * ME / hwp**2)
+    s = [L.orc_dedx_coll(Z, A, rho, I, charge, T, cut) for T in (1e3, 1e4, 1e5, 1e6)]
+    dev = np.abs(np.array(s) / plateau - 1)
+    assert dev[-1] < 1e-6
+    assert np.all(np.diff(dev) <= 0)  # approaches the plateau monotonically
+
+
 def test_gauss_legendre(oracle_mod):
     x, w = oracle_mod.gauss_legendre(16)
     xr, wr = np.polynomial.legendre.leggauss(16)
