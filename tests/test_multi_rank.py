@@ -20,10 +20,10 @@ def _free_port():
     return p
 
 
-def _setup():
+def _setup(n=24):
     s = W.calo_setup()
-    prim = W.multi_primaries(24, 1, 5, 200.0, 20.0, seed=41)
-    ids = np.arange(100, 124, dtype=np.uint64)
+    prim = W.multi_primaries(n, 1, 5, 200.0, 20.0, seed=41)
+    ids = np.arange(100, 100 + n, dtype=np.uint64)
     return s, prim, ids
 
 
@@ -33,12 +33,12 @@ def _engine(s):
     return lambda prim, ids: o.run(prim, len(ids), ids, n_threads=2)
 
 
-def _worker(rank, world, port, out_dir):
+def _worker(rank, world, port, out_dir, n=24):
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    s, prim, ids = _setup()
+    s, prim, ids = _setup(n)
     H, S = shard.run_sharded(_engine(s), prim, ids, rank, world)
     np.save(os.path.join(out_dir, f"h{rank}.npy"), H)
     np.save(os.path.join(out_dir, f"s{rank}.npy"), S)
@@ -60,6 +60,21 @@ def test_two_gloo_ranks_equal_single_run(tmp_path):
     world = 2
     mp.spawn(_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
     s, prim, ids = _setup()
+    H1, S1 = shard.run_sharded(_engine(s), prim, ids, 0, 1)
+    for r in range(world):
+        assert np.array_equal(np.load(tmp_path / f"h{r}.npy"), H1)
+        assert np.array_equal(np.load(tmp_path / f"s{r}.npy"), S1)
+
+
+def test_rank_without_events(tmp_path):
+    """Three gloo ranks and two events: one rank's shard is empty, and the
+    gathered results still equal the single-process run."""
+    import oracle
+    oracle.build()
+    world, n = 3, 2
+    assert min(len(p) for p in shard.partition_by_cost(shard.event_costs(_setup(n)[1], n), world)) == 0
+    mp.spawn(_worker, args=(world, _free_port(), str(tmp_path), n), nprocs=world, join=True)
+    s, prim, ids = _setup(n)
     H1, S1 = shard.run_sharded(_engine(s), prim, ids, 0, 1)
     for r in range(world):
         assert np.array_equal(np.load(tmp_path / f"h{r}.npy"), H1)
