@@ -300,3 +300,26 @@ def test_deposits_are_scored_in_the_volume_traversed(oracle_mod):
     hist, summ = o.run(one_primary(1, T0, [0.1, 0.2, -1.0], [0, 0, 1]), 1, [0])
     assert np.count_nonzero(expected) > 10
     np.testing.assert_allclose(hist[0, : o.n_bins], expected, rtol=1e-12, atol=0)
+
+
+def test_closed_channel_is_a_null_interaction(oracle_mod):
+    """Between the node below the pair threshold (Sigma = 0) and the one above
+    it, the interpolated Sigma_pair is positive below 2 m: the photon can
+    choose pair production where the channel is closed, and the step is
+    then a null interaction (the photon goes on unchanged, nothing is
+    deposited or produced, the step is counted)."""
+    s = W.slab_setup(mask=4, thickness=1e4)
+    s.world[3:9] = [-1e5, -1e5, -1e5, 1e5, 1e5, 1e5]
+    s.world[1] = s.world[2] = 1e4
+    o = make(oracle_mod, s)
+    g = o.grid()
+    n = int(np.searchsorted(g, 2 * ME))
+    assert o.table(0, 0, 2)[n - 1] == 0.0 and o.table(0, 0, 2)[n] > 0.0
+    T = 0.5 * (max(g[n - 1], s.physics[0]) + 2 * ME)
+    for uid in range(1, 201):
+        t0 = np.array([0, T, 0, 0, 5e3, 0, 0, 1, 0, 0], float)
+        t, sec, info = o.step_one(t0.copy(), uid, 3)
+        assert info[3] == 1 and int(info[4]) == oracle_mod.PAIR and info[5] == 1
+        assert len(sec) == 0 and info[1] == 0.0
+        assert t[1] == T and list(t[5:8]) == [0, 0, 1] and t[9] == 1
+        assert t[4] == pytest.approx(5e3 + info[0], rel=1e-15)
