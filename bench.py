@@ -444,7 +444,7 @@ def gpu_arm(args):
 
 
 def diagnostics(args, emt, setup, prim, ids, cfg, device):
-    """Sec. 4's diagnostics of one untimed run of the workload: tracks in
+    """Sec. 3.2's diagnostics of one untimed run of the workload: tracks in
     flight, interactions, deferred and held copies and device time per step
     (plain driver), and the steps-per-track histogram by particle type."""
     nb = 4096

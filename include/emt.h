@@ -3,18 +3,18 @@
  *
  * The library runs the per-step Monte Carlo transport loop for photons,
  * electrons and positrons described in arXiv:2203.09467 (Celeritas):
- * cross sections from tabulated log-spaced grids (Sec. 3.2, "all particle
- * types use tabulated discrete interaction cross sections calculated
- * simultaneously in a single kernel"), continuous slowing down and energy
- * cutoffs (Sec. 3.2 list of capabilities), the six electromagnetic models
+ * cross sections from tabulated log-spaced grids (Sec. 2.2: the
+ * discrete cross sections of every particle type come from tables and are
+ * evaluated together in one kernel), continuous slowing down and energy
+ * cutoffs (Sec. 2.2 list of capabilities), the six electromagnetic models
  * of Table 1 (Klein-Nishina, Bethe-Heitler, photoelectric, bremsstrahlung,
  * Moller-Bhabha, two-photon annihilation), straight-line and uniform-field
- * propagation through layered-box or concentric-cylinder geometry (Sec. 3.3;
- * the cylinders are Sec. 4's CMS-like test problem), secondary
- * allocation with a capacity-bounded device stack (Sec. 3.1, "function-like
- * stack allocator ... atomic addition", with out-of-memory handled without
- * breaking reproducibility), and scoring in device kernels instead of host
- * callbacks (Sec. 3.4).  The call sequence follows the paper's statement of
+ * propagation through layered-box or concentric-cylinder geometry (Sec. 2.3;
+ * the cylinders are Sec. 3.2's CMS-like test problem), secondary
+ * allocation with a capacity-bounded device stack (Sec. 2.1:
+ * secondaries are reserved from a stack by an atomic add, and running out
+ * of room must not break reproducibility), and scoring in device kernels instead of host
+ * callbacks (Sec. 2.4).  The call sequence follows the paper's statement of
  * the problem: load materials and physics tables, load geometry, submit
  * primaries for many concurrent events, step until done, read the scores.
  *
@@ -113,7 +113,7 @@ typedef struct emt_options {
     void* cuda_stream;     /* cudaStream_t to use, or NULL for a context-owned stream */
     void* device_pool;     /* caller-owned device memory, or NULL: see emt_pool_bytes */
     size_t pool_bytes;
-    int32_t step_hist_bins; /* > 0: keep the steps-per-track histogram (Sec. 4 diagnostics),
+    int32_t step_hist_bins; /* > 0: keep the steps-per-track histogram (Sec. 3.2 diagnostics),
                                emt_read_step_hist; 0: off (no cost) */
     int32_t select_policy;  /* EMT_SELECT_*: which tracks step when more than max_active are in flight */
     int64_t max_active;     /* > 0: at most this many tracks step per iteration, the others are
@@ -125,8 +125,8 @@ typedef struct emt_options {
                                0: off */
 } emt_options;
 
-/* Track selection (Sec. 4: "preferentially selecting lower-energy particles
- * for tracking ... could reduce the total capacity requirement").  Held
+/* Track selection (Sec. 3.2: stepping the low-energy tracks first may lower
+ * the number of track slots a problem needs).  Held
  * tracks keep their step counter, so they draw the same random numbers
  * when they step later: results do not depend on the policy or the budget
  * (up to the summation order of deposits).
@@ -151,15 +151,15 @@ emt_status emt_create(const emt_options* opt, emt_ctx** out);
 void emt_destroy(emt_ctx* ctx);
 const char* emt_last_error(const emt_ctx* ctx);
 
-/* Materials (Sec. 3.2: material-dependent properties; single element per
- * material, as in the paper's demonstration, Sec. 4 caveats).
+/* Materials (Sec. 2.2: material-dependent properties; single element per
+ * material, as in the paper's demonstration, Sec. 3.2 caveats).
  * rho_g_cm3 == 0 marks vacuum.  bk_MeV is the K-shell binding energy used by
  * the photoelectric model. */
 typedef struct emt_material {
     double Z, A_g_mol, rho_g_cm3, I_eV, bk_MeV;
 } emt_material;
 
-/* Physics options (Sec. 3.2: processes, models and energy cutoffs).
+/* Physics options (Sec. 2.2: processes, models and energy cutoffs).
  * cut_MeV: production and tracking cuts for gamma, e-, e+.
  * Tables are built on the device on the grid
  * E_n = grid_lo * 10^(n / bins_per_decade), n = 0..bpd*log10(hi/lo). */
@@ -176,7 +176,7 @@ typedef struct emt_physics {
  * device (host: mats[n], phys).  Replaces earlier tables.  n in [1, 16]. */
 emt_status emt_load_materials(emt_ctx* ctx, const emt_material* mats, int32_t n, const emt_physics* phys);
 
-/* Layered-box geometry (Sec. 3.3): layers stacked along +z from z0, each
+/* Layered-box geometry (Sec. 2.3): layers stacked along +z from z0, each
  * |x| <= half_x, |y| <= half_y, inside the world box [lo, hi]; the world
  * outside the stack is vacuum.  material -1 means vacuum.  score_bin is
  * the histogram column of the layer (-1: not scored in the histogram). */
@@ -186,7 +186,7 @@ typedef struct emt_layer {
     double thickness_cm;
 } emt_layer;
 
-/* Geometry kinds (Sec. 3.3; the paper's navigators are VecGeom and ORANGE,
+/* Geometry kinds (Sec. 2.3; the paper's navigators are VecGeom and ORANGE,
  * a CSG of quadric surfaces, which this library replaces by two volume
  * kinds with exact logical volume indices):
  * LAYERS: layer i is the slab zb[i] <= z < zb[i+1] (zb[0] = z0, zb[i+1] =
@@ -196,7 +196,7 @@ typedef struct emt_layer {
  *   (radii accumulated from z0, which must be 0; the first layer is a solid
  *   cylinder) for |z| <= half_z; leaving the outermost shell or the end
  *   planes leaves the world (the envelope is the world).  half_x, half_y,
- *   lo and hi are ignored.  This is the geometry of Sec. 4's test problem
+ *   lo and hi are ignored.  This is the geometry of Sec. 3.2's test problem
  *   (six single-element shells out to 375 cm). */
 #define EMT_GEOM_LAYERS 0
 #define EMT_GEOM_CYLINDERS 1
@@ -211,7 +211,7 @@ typedef struct emt_world {
     int32_t n_bins;           /* histogram width (<= options.max_bins) */
     int32_t geometry;         /* EMT_GEOM_* */
     int32_t score_z;          /* 0: bin = the layer's score_bin; 1: n_bins equal bins of z
-                                 over [score_z_lo, score_z_hi) (Sec. 4 tallies the
+                                 over [score_z_lo, score_z_hi) (Sec. 3.2 tallies the
                                  deposition along z) */
     double half_z_cm;         /* CYLINDERS: half-length */
     double score_z_lo_cm, score_z_hi_cm;
@@ -260,7 +260,7 @@ typedef struct emt_run_stats {
  * (<= 0: no limit) iterations have run.  stats may be NULL. */
 emt_status emt_run(emt_ctx* ctx, int32_t max_iterations, emt_run_stats* stats);
 
-/* Per-step diagnostics (Sec. 4, tracks in flight and time per step): as
+/* Per-step diagnostics (Sec. 3.2, tracks in flight and time per step): as
  * emt_run with the plain driver, recording for each iteration the photons
  * and charged tracks in flight at its start, the tracks queued for an
  * interaction (split schedule; -1 under the fused one), the track-steps
@@ -280,7 +280,7 @@ typedef struct emt_step_record {
 emt_status emt_run_traced(emt_ctx* ctx, int32_t max_iterations, emt_run_stats* stats, emt_step_record* rec,
                           int32_t cap, int32_t* n_rec);
 
-/* Steps-per-track histogram (Sec. 4: steps per track by particle type),
+/* Steps-per-track histogram (Sec. 3.2: steps per track by particle type),
  * kept when emt_options.step_hist_bins > 0: host out[3][step_hist_bins],
  * counts of finished tracks by type (0 gamma, 1 e-, 2 e+) and number of
  * steps, tracks of step_hist_bins - 1 or more steps in the last bin,
@@ -312,7 +312,7 @@ int32_t emt_events_in_flight(const emt_ctx* ctx);
 int64_t emt_tracks_in_flight(const emt_ctx* ctx);
 
 /* ---------------------------------------------------------------------
- * Serving (Sec. 3.4: many concurrent events keep the device busy; Sec. 4:
+ * Serving (Sec. 2.4: many concurrent events keep the device busy; Sec. 3.2:
  * workflows must batch events).  emt_serve replays a stream of event
  * requests against one context in real time (arrival times divided by
  * time_scale) and returns when every request has been answered.

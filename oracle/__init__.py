@@ -1,4 +1,4 @@
-"""FP64 CPU oracle of the EM transport loop (arXiv:2203.09467, Secs. 3-4).
+"""FP64 CPU oracle of the EM transport loop (arXiv:2203.09467, Secs. 2.1-3.2).
 
 TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
 CPU-baseline leg of the benchmark import this package.  It shares no code

@@ -7,7 +7,7 @@
  * leg of the benchmark, and from nothing else.  It shares no code with the
  * CUDA path.
  *
- * The paper names the physics models (Sec. 3.2, Table 1) and capabilities
+ * The paper names the physics models (Sec. 2.2, Table 1) and capabilities
  * (material properties, continuous slowing down, competing discrete
  * processes, secondaries, energy cutoffs) but prints no formula.  Every
  * formula below is a textbook closed form, cited at its definition in

@@ -1,8 +1,7 @@
 // emt_serve.cu -- event-request serving loop on top of the public C ABI.
 //
-// The paper asks for many concurrent events to fill the device (Sec. 3.4;
-// Sec. 4: "experimental workflows may need to batch multiple events
-// together").  Two schedules over one context (whose track state stays on
+// The paper asks for many concurrent events to fill the device (Sec. 2.4;
+// Sec. 3.2: workflows will have to group several events into one batch).  Two schedules over one context (whose track state stays on
 // the device across requests):
 //   continuous : requests that arrive while others are in flight are
 //                admitted as soon as event slots and track slots allow

@@ -1,7 +1,7 @@
 // emt_tables.cu -- builds every cross-section, stopping-power and range
 // table on the device, in FP64 (compiled with --fmad=false).
 //
-// Tables are tabulated on the log grid E_n = E_lo 10^(n/bpd) (Sec. 3.2: all
+// Tables are tabulated on the log grid E_n = E_lo 10^(n/bpd) (Sec. 2.2: all
 // particle types use tabulated cross sections).  The paper prints no model
 // formula; these are the textbook closed forms:
 //   radiation length   Tsai 1974 (PDG review "Passage of particles through

@@ -1,7 +1,7 @@
 """Event sharding across ranks (one process per GPU).
 
 Events are independent (the paper's domain replication: events are
-decomposed across MPI ranks, Sec. 3.1), so a multi-GPU run partitions the
+decomposed across MPI ranks, Sec. 2.1), so a multi-GPU run partitions the
 events, transports each shard on its own GPU with no exchange while
 stepping, and gathers the per-event results once at the end.
 """

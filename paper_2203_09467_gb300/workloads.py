@@ -5,7 +5,7 @@ random primaries of each workload); it contains none of the transport
 arithmetic, and both the GPU library and the CPU oracle are fed from it.
 
 Workloads (synthetic calorimeter workloads, plus the paper's own test
-problem of Sec. 4 with its unstated dimensions read as below):
+problem of Sec. 3.2 with its unstated dimensions read as below):
 
   slab      1,000 events x one 100 MeV e- along +z into a 5 cm Pb slab,
             20x20 cm, no field, one score bin.
@@ -17,7 +17,7 @@ problem of Sec. 4 with its unstated dimensions read as below):
   batched   256 events of 1-64 primaries, e-/e+/gamma, 0.1-100 GeV
             log-uniform, on the calo_field geometry.
   served    Poisson arrivals; 1-100 primaries per event, 1-50 GeV.
-  cms       the paper's verification problem (Sec. 4): six concentric
+  cms       the paper's verification problem (Sec. 3.2): six concentric
             cylindrical shells about the z axis out to 375 cm, each one
             element (vacuum, Si, Pb, C, Ti, Fe), no field; 100 events x 1000
             photons of 1 GeV from an isotropic point source at the origin;

@@ -1,4 +1,4 @@
-"""The concentric-cylinder geometry of the paper's Sec. 4 test problem on
+"""The concentric-cylinder geometry of the paper's Sec. 3.2 test problem on
 the GPU (through the C ABI) against the FP64 oracle: single steps from
 random states in every shell, whole events (straight and in a solenoid
 field, both step schedules), deposition scored along z, the
@@ -112,7 +112,7 @@ def test_single_step_parity_cylinders(emt, oracle_mod):
 
 @pytest.mark.parametrize("schedule", ["fused", "split"])
 def test_cms_event_parity(emt, oracle_mod, schedule):
-    """Sec. 4's problem at reduced size (12 events x 50 photons of 1 GeV):
+    """Sec. 3.2's problem at reduced size (12 events x 50 photons of 1 GeV):
     z profile, totals, step and track counts and the steps-per-track
     histogram by particle type all match the oracle."""
     s = W.cms_setup()
@@ -172,7 +172,7 @@ def test_step_trace(emt):
 
 
 def test_cms_mixed_statistical(emt, oracle_mod):
-    """Mixed precision on Sec. 4's problem: totals, the z profile (Hotelling
+    """Mixed precision on Sec. 3.2's problem: totals, the z profile (Hotelling
     T^2 over groups of bins) and the mean steps per track of each particle
     type agree with the FP64 oracle within their statistical errors."""
     from stats_util import profile_test, mean_test

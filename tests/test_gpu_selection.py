@@ -1,4 +1,4 @@
-"""Track selection (an active budget per step, Sec. 4's low-energy-first
+"""Track selection (an active budget per step, Sec. 3.2's low-energy-first
 suggestion): the budget is respected exactly, held tracks change no result
 (per-event deposits within the summation-order tolerance, step and track
 counts identical to an unlimited run and to the FP64 oracle), and

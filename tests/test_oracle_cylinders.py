@@ -1,4 +1,4 @@
-"""Pins of the oracle's cylinder-shell geometry (the paper's Sec. 4 test
+"""Pins of the oracle's cylinder-shell geometry (the paper's Sec. 3.2 test
 problem: concentric single-element shells about the z axis), of scoring
 along z and of the steps-per-track histogram.
 

@@ -228,7 +228,7 @@ def test_shower_maximum_is_plausible(oracle_mod):
 @pytest.mark.parametrize("ptype,mask,node", [(0, 7, 40), (0, 7, 32), (1, 24, 40), (2, 56, 40), (2, 56, 28)])
 def test_process_selection_frequencies(oracle_mod, ptype, mask, node):
     """The model of an interaction is chosen with probability Sigma_i /
-    Sigma_tot (competing processes, Sec. 3.2): at a grid node the
+    Sigma_tot (competing processes, Sec. 2.2): at a grid node the
     interpolated Sigma's are the table entries, so the counts over many
     independent draw streams are multinomial with those probabilities."""
     s = W.slab_setup(mask=mask, thickness=1e4)
