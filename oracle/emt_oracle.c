@@ -1,7 +1,7 @@
 /*
  * emt_oracle.c -- plain, slow, FP64 CPU oracle of the per-step EM transport
- * loop described in arXiv:2203.09467 (Sec. 3.1 "one thread per track";
- * Sec. 3.2 physics, Table 1; Sec. 3.3 geometry and fields; Sec. 4
+ * loop described in arXiv:2203.09467 (Sec. 2.1 "one thread per track";
+ * Sec. 2.2 physics, Table 1; Sec. 2.3 geometry and fields; Sec. 3.2
  * preliminary results).
  *
  * TEST INFRASTRUCTURE ONLY: called by tests, by the smoke check and by the
@@ -72,7 +72,7 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
     out[3] = c3;
 }
 
-/* Stream keying (a reading; the paper's demo used XORWOW, Sec. 4 caveats):
+/* Stream keying (a reading; the paper's demo used XORWOW, Sec. 3.2 caveats):
  *   key = (lo32(event_id), hi32(event_id) ^ seed)
  *   ctr = (lo32(uid), hi32(uid), step, j >> 1)
  * draw j uses output words 2(j&1) (low) and 2(j&1)+1 (high) of that block;
@@ -744,12 +744,12 @@ int orc_get_table(const orc_handle* h, int m, int p, int q, double* out)
 }
 
 /* ------------------------------------------------------------------ */
-/* Geometry (a reading of Sec. 3.3: the paper navigates CMS with       */
+/* Geometry (a reading of Sec. 2.3: the paper navigates CMS with       */
 /* VecGeom or ORANGE, a CSG of quadric surfaces; here two simple kinds */
 /* of volumes with exact logical volume indices).                      */
 /* Layers: slabs stacked along +z from z0 inside |x|<=hx, |y|<=hy;     */
 /* volume -1 is the vacuum of the world box; -2 is outside the world.  */
-/* Cylinders: concentric shells about the z axis (Sec. 4's test        */
+/* Cylinders: concentric shells about the z axis (Sec. 3.2's test        */
 /* problem), shell i spanning zb[i] <= rho < zb[i+1] and |z| <= half_z,*/
 /* zb[0] = 0; leaving the outermost shell or the end planes leaves the */
 /* world (-2).                                                         */
@@ -1352,13 +1352,17 @@ int orc_sample(int process, double E, double cut_e, double cut_g, uint32_t seed,
 /* h <= sqrt(8 r delta) (sagitta <= delta); after each substep the     */
 /* chord is tested against the current volume, and a crossing at chord */
 /* fraction f repeats the substep with h f and snaps onto the plane.   */
-/* (Sec. 3.3 says only that propagation is on-device with selectable   */
+/* (Sec. 2.3 says only that propagation is on-device with selectable   */
 /* integrators; this is a reading.)                                    */
 /* ------------------------------------------------------------------ */
-/* A step in a field takes at most MAX_SUBSTEPS substeps of h_max (and at
- * most max_field_step); a step shortened this way ends without an
- * interaction and the track continues at its next step (a reading: it
- * bounds the work of one step of a looping low-energy track). */
+/* A step in a field is a whole number n of equal RK4 substeps of at most
+ * h_max: n = ceil(s / h_max) substeps of s / n for a step limit s up to
+ * MAX_SUBSTEPS h_max (and up to max_field_step).  A longer step is cut to
+ * exactly MAX_SUBSTEPS substeps of h_max and ends without an interaction;
+ * the track continues at its next step (a reading: it bounds the work of
+ * one step of a looping low-energy track).  The cut step's substep count
+ * is set, not recomputed from s / h_max, whose rounding would otherwise
+ * decide between MAX_SUBSTEPS and MAX_SUBSTEPS + 1 substeps. */
 #define MAX_SUBSTEPS 100
 
 /* The RK4 arithmetic is written with fused multiply-adds where a product
@@ -1398,20 +1402,14 @@ static void rk4(const orc_handle* h, double kq, const double x[3], const double 
     for (int i = 0; i < 3; ++i) uo[i] = uo[i] / n;
 }
 
-/* propagate a charged track along the field for at most smax;
- * returns path length; *bnd receives the crossing (or next = 0x7fff) */
+/* propagate a charged track along the field by n substeps of length hs
+ * (or up to the first boundary crossing); returns the path length;
+ * *bnd receives the crossing */
 static double propagate_field(const orc_handle* h, int charge, double T, int vol, double x[3], double u[3],
-                              double smax, exit_t* bnd, int* crossed)
+                              int n, double hs, exit_t* bnd, int* crossed)
 {
     double p = sqrt(T * (T + 2.0 * ME));
     double kq = charge * FIELD_C / p;
-    double bmag = sqrt(h->B[0] * h->B[0] + h->B[1] * h->B[1] + h->B[2] * h->B[2]);
-    double r = p / (FIELD_C * bmag);
-    double hmax = sqrt(8.0 * r * h->rk_delta);
-    double ns = ceil(smax / hmax);
-    if (ns < 1.0) ns = 1.0;
-    double hs = smax / ns;
-    int n = (int)ns;
     double s = 0.0;
     *crossed = 0;
     for (int i = 0; i < n; ++i) {
@@ -1607,18 +1605,25 @@ static void step_track(const orc_handle* h, uint64_t event_id, track_t* tr, tall
             smax = h->max_field_step;
             interact = 0;
         }
-        /* at most MAX_SUBSTEPS RK4 substeps per step (the substep length
-         * h_max below is the one propagate_field uses) */
+        /* substeps of at most h_max = sqrt(8 r delta), r = p / (c |B|);
+         * at most MAX_SUBSTEPS of them */
         double pm = sqrt(tr->T * (tr->T + 2.0 * ME));
         double bmag = sqrt(h->B[0] * h->B[0] + h->B[1] * h->B[1] + h->B[2] * h->B[2]);
         double hmax = sqrt(8.0 * (pm / (FIELD_C * bmag)) * h->rk_delta);
-        double cap = MAX_SUBSTEPS * hmax;
-        if (smax > cap) {
-            smax = cap;
+        int nsub;
+        double hs;
+        if (smax > MAX_SUBSTEPS * hmax) {
+            nsub = MAX_SUBSTEPS;
+            hs = hmax;
             interact = 0;
+        } else {
+            double ns = ceil(smax / hmax);
+            if (ns < 1.0) ns = 1.0;
+            nsub = (int)ns;
+            hs = smax / ns;
         }
         int crossed = 0;
-        s = propagate_field(h, tr->type == 1 ? -1 : 1, tr->T, tr->vol, tr->x, tr->u, smax, &e, &crossed);
+        s = propagate_field(h, tr->type == 1 ? -1 : 1, tr->T, tr->vol, tr->x, tr->u, nsub, hs, &e, &crossed);
         boundary = crossed;
         if (boundary) interact = 0;
     }
@@ -1813,7 +1818,7 @@ static void run_event(const orc_handle* h, uint64_t event_id, int n, const int* 
             for (int k = r.n_sec - 1; k >= 0; --k) push(&st, &r.sec[k]);
             if (!r.alive) break;
         }
-        /* steps per track by particle type (Sec. 4 diagnostics) */
+        /* steps per track by particle type (Sec. 3.2 diagnostics) */
         if (step_hist) {
             uint32_t b = t.step < (uint32_t)(step_bins - 1) ? t.step : (uint32_t)(step_bins - 1);
             step_hist[(size_t)t.type * step_bins + b] += 1;

@@ -1,6 +1,6 @@
 // emt_device.cuh -- device-side data layout, random streams, table
 // lookups, navigation, field propagation and interaction samplers of the
-// EM transport step (arXiv:2203.09467, Secs. 3.1-3.3).
+// EM transport step (arXiv:2203.09467, Secs. 2.1-2.3).
 //
 // Templated on the physics real type R: double for the FP64 path (built
 // with --fmad=false so every expression rounds exactly as written) and
@@ -604,12 +604,18 @@ __device__ __forceinline__ Exit nav_exit_layers(const Params<R>& p, int vol, con
         // select the candidates that can be the minimum (within 1e-5 of the
         // smallest estimate); only those are divided in FP64, in the same
         // order and with the same strict comparison, so the result is the
-        // one all three FP64 divisions would give.
+        // one all three FP64 divisions would give.  An estimate is trusted
+        // only where its divisor is in the FP32 normal range: a nonzero
+        // direction component below it truncates to 0 and its estimate
+        // (infinite, or 0/0 from a point exactly on the wall) says nothing,
+        // so that candidate is always divided.  The numerator (a distance
+        // within the geometry) cannot overflow the FP32 range.
         const int L = p.n_layers;
         double pl[3], diff[3];
         int nx[3];
         bool has[3];
         float tf[3];
+        bool sure[3];
         has[2] = nonzero(d[2]);
         if (gt_zero(d[2])) {
             pl[2] = p.zb[vol + 1];
@@ -629,7 +635,9 @@ __device__ __forceinline__ Exit nav_exit_layers(const Params<R>& p, int vol, con
         for (int a = 0; a < 3; ++a) {
             if (!has[a]) continue;
             diff[a] = pl[a] - x[a];
-            tf[a] = d2f_est(diff[a]) / d2f_est(d[a]);
+            const float df = d2f_est(d[a]);
+            sure[a] = df != 0.0f;
+            tf[a] = d2f_est(diff[a]) / df;
             tmin = fminf(tmin, tf[a]);
         }
         // a non-finite smallest estimate (a direction component below the
@@ -640,7 +648,7 @@ __device__ __forceinline__ Exit nav_exit_layers(const Params<R>& p, int vol, con
 #pragma unroll
         for (int oi = 0; oi < 3; ++oi) {
             const int a = order[oi];
-            if (!has[a] || !(tf[a] <= thr)) continue;
+            if (!has[a] || (sure[a] && !(tf[a] <= thr))) continue;
             double t = diff[a] / d[a];
             if (t < e.t) {
                 e.t = t;
@@ -762,8 +770,10 @@ __device__ __forceinline__ void rk4(const Params<R>& p, R kq, const double x[3],
 // at least the margin, so skipping it changes no result.
 constexpr double kChordMargin = 1e-6;  // cm
 
-// A step in a field takes at most kMaxSubsteps substeps of h_max (and at
-// most max_field_step); a step shortened this way ends without an
+// A step in a field is n equal RK4 substeps: n = ceil(s / h_max) of s / n
+// for a step limit s up to kMaxSubsteps h_max (and up to max_field_step);
+// a longer step is exactly kMaxSubsteps substeps of h_max (the count is
+// set, not recomputed from a rounded quotient) and ends without an
 // interaction: it bounds the work of one step of a looping track.
 constexpr int kMaxSubsteps = 100;
 
@@ -812,25 +822,18 @@ __device__ __forceinline__ bool chord_inside(const Params<R>& p, int vol, const 
     return false;
 }
 
-// substeps of equal length smax/ceil(smax/hmax), hmax = sqrt(8 r delta);
-// the chord of each substep is tested against the current volume and a
-// crossing at fraction f repeats the substep with h f, snapped onto the
-// plane.  Returns the path length.
+// n substeps of length hs (the caller derives both from h_max); the chord
+// of each substep is tested against the current volume and a crossing at
+// fraction f repeats the substep with h f, snapped onto the plane.
+// Returns the path length.
 template <int G, typename R>
-__device__ __forceinline__ double propagate_field(const Params<R>& p, int charge, double T, int vol, double x[3],
-                                                  R u[3], double smax, Exit* bnd, bool* crossed)
+__device__ __forceinline__ double propagate_field(const Params<R>& p, int charge, double pm, int vol, double x[3],
+                                                  R u[3], int n, double hs, Exit* bnd, bool* crossed)
 {
-    double pm = sqrt(T * (T + 2.0 * kMe));
     double kq = charge * kFieldC / pm;
-    double r = pm / (kFieldC * p.bmag);
-    double hmax = sqrt(8.0 * r * p.rk_delta);
-    double ns = ceil(smax / hmax);
-    if (ns < 1.0) ns = 1.0;
-    double hs = smax / ns;
-    long long n = (long long)ns;
     double s = 0.0;
     *crossed = false;
-    for (long long i = 0; i < n; ++i) {
+    for (int i = 0; i < n; ++i) {
         double x1[3], c[3];
         R u1[3];
         rk4(p, R(kq), x, u, R(hs), x1, u1);

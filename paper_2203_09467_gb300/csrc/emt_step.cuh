@@ -1,7 +1,7 @@
 // emt_step.cuh -- one transport step of every track in flight, as one
-// kernel launch (arXiv:2203.09467 Sec. 3.1: one thread per track; Sec. 3.2:
+// kernel launch (arXiv:2203.09467 Sec. 2.1: one thread per track; Sec. 2.2:
 // cross sections, continuous loss, discrete interactions, secondaries and
-// cutoffs; Sec. 3.3: propagation; Sec. 3.4: scoring in kernels).
+// cutoffs; Sec. 2.3: propagation; Sec. 2.4: scoring in kernels).
 //
 // Layout and scheduling (the paper's own design launches one kernel per
 // model from the host; this one is GB300-first):
@@ -19,7 +19,7 @@
 //    sorted by model into shared memory; phase B runs the samplers over the
 //    sorted records, so a warp executes one model (or two, at a group
 //    boundary) instead of every model its lanes happened to select.  This
-//    is the paper's one-kernel-per-model idea (Sec. 3.2) done inside one
+//    is the paper's one-kernel-per-model idea (Sec. 2.2) done inside one
 //    launch, without a round trip through device memory.
 //  * Output slots are reserved once per warp: a shuffle prefix sum over the
 //    lanes' photon and charged output counts and one atomicAdd per type.
@@ -27,7 +27,7 @@
 //    is copied unchanged (deferred, see k_step).  A deferred track keeps its
 //    step counter, so its random stream and every result are unchanged (the
 //    paper's out-of-memory robustness without loss of reproducibility,
-//    Sec. 3.1).
+//    Sec. 2.1).
 #pragma once
 
 #include "emt_device.cuh"
@@ -263,17 +263,25 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
             smax = p.max_field_step;
             interact = false;
         }
-        // at most kMaxSubsteps substeps of h_max per step
+        // substeps of at most h_max = sqrt(8 r delta), r = p / (c |B|); at
+        // most kMaxSubsteps of them
         const double Td = to_d(t.T);
         const double pm = sqrt(Td * (Td + 2.0 * kMe));
         const double hmax = sqrt(8.0 * (pm / (kFieldC * p.bmag)) * p.rk_delta);
-        const double cap = kMaxSubsteps * hmax;
-        if (smax > cap) {
-            smax = cap;
+        int nsub;
+        double hs;
+        if (smax > kMaxSubsteps * hmax) {
+            nsub = kMaxSubsteps;
+            hs = hmax;
             interact = false;
+        } else {
+            double ns = ceil(smax / hmax);
+            if (ns < 1.0) ns = 1.0;
+            nsub = (int)ns;
+            hs = smax / ns;
         }
         bool crossed = false;
-        s = propagate_field<G>(p, t.type == 1 ? -1 : 1, Td, t.vol, t.x, t.u, smax, &e, &crossed);
+        s = propagate_field<G>(p, t.type == 1 ? -1 : 1, pm, t.vol, t.x, t.u, nsub, hs, &e, &crossed);
         boundary = crossed;
     }
     if (boundary) interact = false;
@@ -536,7 +544,7 @@ __device__ __forceinline__ void emit(const Params<R>& p, const Tracks<R>& qo, Co
     }
 }
 
-// Track selection (the paper's Sec. 4: preferring low-energy tracks keeps
+// Track selection (the paper's Sec. 3.2: preferring low-energy tracks keeps
 // the number of tracks in flight, and so the capacity needed, down).  The
 // lowest-energy class c* whose cumulative count over the input reaches
 // max_active, and the quota of tracks of class c* that may still step.

@@ -6,10 +6,8 @@ steps-per-track histogram and the per-step trace.
 
 Tolerances as in test_gpu_parity: the FP64 path repeats the oracle's
 arithmetic in the same order, so positions agree to rounding, step and
-track counts exactly, deposits to 1e-9 of the event energy (summation
-order of the atomics); in the field, per-bin deposits to 1e-6 of the event
-energy (a last-bit difference of a transcendental function can change the
-integer number of RK4 substeps of a step)."""
+track counts exactly, deposits (totals and every bin) to 1e-9 of the event
+energy (summation order of the atomics), in the field too."""
 import numpy as np
 import pytest
 
@@ -132,7 +130,7 @@ def test_cms_field_parity(emt, oracle_mod):
     prim = W.cms_primaries(n, 25, seed=9)
     hist, summ, st, _ = gpu_run(emt, s, prim, n, schedule="split")
     ohist, osumm = oracle_of(oracle_mod, s).run(prim, n, np.arange(n))
-    check_events(summ, osumm, hist, ohist, frac=0.99, bin_tol=1e-6)
+    check_events(summ, osumm, hist, ohist)
 
 
 def test_layers_scored_along_z(emt, oracle_mod):
@@ -187,7 +185,7 @@ def test_cms_mixed_statistical(emt, oracle_mod):
     d, se = mean_test(summ[:, 0], osumm[:, 0])
     assert abs(d) < 4 * se + 1e-6 * osumm[:, 0].mean()
     t2, dof, p = profile_test(hist, ohist)
-    assert p > 1e-3, (t2, dof, p)
+    assert p > 0.01, (t2, dof, p)
     steps = np.arange(nb)
     for k in range(3):
         m_gpu = (sh[k] * steps).sum() / sh[k].sum()

@@ -54,7 +54,7 @@ def test_mixed_matches_oracle_statistically(emt, oracle_mod, workload):
     assert abs(d) < 4 * se + 1e-6 * so[:, 0].mean(), (d, se)
     # longitudinal profile
     t2, dof, p = profile_test(hm, ho)
-    assert p > 1e-3, (t2, dof, p)
+    assert p > 0.01, (t2, dof, p)
     # steps per event agree to within a few percent on average
     assert abs(sm[:, 4].mean() / so[:, 4].mean() - 1) < 0.03
 
@@ -86,7 +86,7 @@ def test_mixed_error_statement(emt, oracle_mod):
           f"steps/event {sm[:, 4].mean():.0f} vs {so[:, 4].mean():.0f}")
     assert abs(d) < 4 * se + 1e-6 * so[:, 0].mean()
     assert abs(dfr) < 4 * sefr
-    assert p > 1e-3
+    assert p > 0.01
     assert led.max() < 1e-5
 
 

@@ -5,15 +5,15 @@ Rayleigh scattering (screened-atom form factor): the Rayleigh table, single
 steps from random states, whole events (FP64, per event) and mixed
 precision (statistically).
 
-Tolerances: single steps as in test_gpu_parity.  Whole events: every e+-
-step now goes through log, sqrt, sin and cos, whose last bits differ between
-CUDA and libm; a 1e-16 change of direction, carried over the hundreds of
-steps of an event, can move a later boundary or cut decision, after which
-the event's history differs (measured: 2 to 6 of 100 events of 2 GeV, about
-4,700 steps each).  So the event-level bar is 90% of events identical
-(totals to 1e-9 of the event energy, identical step counts), with the
-longitudinal profile of all events agreeing statistically; single steps
-keep the strict bar."""
+Tolerances: single steps as in test_gpu_parity.  Whole events: totals and
+every layer to 1e-9 of the event energy on >= 99.9% of events, with and
+without multiple scattering.  With multiple scattering every e+- step goes
+through log, sqrt, sin and cos, whose last bits differ between CUDA and
+libm; a 1e-16 change of direction can add or remove a step of zero length
+at a corner of a layer (measured on GB300: 1.0-1.3% of 1 GeV events differ
+by a step or a track, with totals and layers still equal to 1e-15), so the
+step and track counts of those events are held to >= 97%.  Without it the
+counts are identical on every event."""
 import numpy as np
 import pytest
 
@@ -96,10 +96,9 @@ def test_single_step_parity_msc(emt, oracle_mod):
     ctx.close()
 
 
-@pytest.mark.parametrize("schedule", ["fused", "split"])
-def test_event_parity_msc_fp64(emt, oracle_mod, schedule):
-    s = W.calo_setup(mask=MASK)
-    n = 200
+def _event_parity(emt, oracle_mod, mask, n, schedule, counts_frac):
+    from stats_util import profile_test
+    s = W.calo_setup(mask=mask)
     prim = W.calo_primaries(n, energy=2000.0)
     ctx = emt.context_for(s, slot_capacity=1 << 22, max_events=n, schedule=schedule)
     ctx.submit(np.arange(n, dtype=np.uint64), prim)
@@ -109,17 +108,30 @@ def test_event_parity_msc_fp64(emt, oracle_mod, schedule):
     ohist, osumm = oracle_of(oracle_mod, s).run(prim, n, np.arange(n))
     e_in = osumm[:, 3]
     rel = np.abs(summ[:, 0] - osumm[:, 0]) / e_in
-    assert (rel <= TOL).mean() >= 0.9, np.sort(rel)[-3:]
+    assert (rel <= TOL).mean() >= 0.999, np.sort(rel)[-3:]
+    hrel = np.abs(hist - ohist).max(axis=1) / e_in
+    assert (hrel <= TOL).mean() >= 0.999, np.sort(hrel)[-3:]
     same = (summ[:, 4] == osumm[:, 4]) & (summ[:, 5] == osumm[:, 5])
-    assert same.mean() >= 0.9
-    # the events whose histories parted still agree statistically
-    from stats_util import profile_test
-    assert profile_test(hist, ohist)[2] > 1e-3
+    assert same.mean() >= counts_frac, same.mean()
+    assert profile_test(hist, ohist)[2] > 0.01
     led = np.abs(summ[:, 3] - summ[:, 0] - summ[:, 1] - summ[:, 2]) / summ[:, 3]
     assert led.max() <= TOL
-    # the options change the showers (more steps: scattered tracks cross more layers)
+    # the options change the showers
     _, plain = oracle_of(oracle_mod, W.calo_setup()).run(prim, n, np.arange(n))
     assert osumm[:, 4].sum() != plain[:, 4].sum()
+
+
+@pytest.mark.parametrize("schedule", ["fused", "split"])
+def test_event_parity_msc_fp64(emt, oracle_mod, schedule):
+    """Every option on, 1,000 events of 2 GeV electrons."""
+    _event_parity(emt, oracle_mod, MASK, 1000, schedule, 0.97)
+
+
+@pytest.mark.parametrize("schedule", ["fused", "split"])
+def test_event_parity_angular_rayleigh_fp64(emt, oracle_mod, schedule):
+    """Angular distributions and Rayleigh scattering without multiple
+    scattering, 1,000 events of 2 GeV electrons: identical counts too."""
+    _event_parity(emt, oracle_mod, 63 + 128 + 256, 1000, schedule, 0.999)
 
 
 def test_msc_mixed_statistical(emt, oracle_mod):
@@ -136,5 +148,5 @@ def test_msc_mixed_statistical(emt, oracle_mod):
     d, se = mean_test(summ[:, 0], osumm[:, 0])
     assert abs(d) < 4 * se + 1e-6 * osumm[:, 0].mean()
     t2, dof, p = profile_test(hist, ohist)
-    assert p > 1e-3, (t2, dof, p)
+    assert p > 0.01, (t2, dof, p)
     assert abs(summ[:, 4].mean() / osumm[:, 4].mean() - 1) < 0.03

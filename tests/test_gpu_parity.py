@@ -173,39 +173,69 @@ def test_event_parity_calo(emt, oracle_mod):
 
 
 def test_event_parity_field_fp64(emt, oracle_mod):
-    """In the field, last-bit differences of exp/log (CUDA vs libm), grown by
-    cancellation (a low-energy lepton from a high-energy photon), can flip
-    the integer number of RK4 substeps of a step and move the track by
-    ~1e-6 cm: energy then shifts by ~1e-6 MeV between neighbouring layers
-    while event totals and step counts still agree.  Totals keep the 1e-9
-    bar; layers are compared at 1e-6 E_in and by the profile test."""
+    """The calorimeter in 2 T with its stated primaries (e-, e+, gamma of
+    1-100 GeV within 10 degrees), 1,000 events in FP64: totals and every
+    layer to 1e-9 of the event energy and identical step and track counts
+    on >= 99.9% of events (measured on GB300: every event, worst 5e-14,
+    also over all 10,000 events of the workload), and the longitudinal
+    profile at p > 0.01."""
     from stats_util import profile_test
     s = W.calo_field_setup()
-    n = 120
-    prim = W.calo_field_primaries(n, e_min=100.0, e_ratio=100.0)
-    hist, summ, st = gpu_run(emt, s, prim, n)
+    n = 1000
+    prim = W.calo_field_primaries(n)
+    hist, summ, st = gpu_run(emt, s, prim, n, slot_capacity=1 << 24)
     ohist, osumm = oracle_of(oracle_mod, s).run(prim, n, np.arange(n))
-    compare_events(summ, osumm, frac=0.99)
-    hrel = np.abs(hist - ohist).max(axis=1) / osumm[:, 3]
-    assert (hrel <= 1e-6).mean() >= 0.99, np.sort(hrel)[-5:]
+    compare_events(summ, osumm, hist, ohist)
     assert profile_test(hist, ohist)[2] > 0.01
 
 
-def test_full_size_calo_sampled(emt, oracle_mod):
-    """The 10,000-event 10 GeV calorimeter in the benchmark's launch
-    configuration; 200 sampled events are recomputed by the oracle, and the
-    ledger is checked on all."""
+def test_full_size_calo(emt, oracle_mod):
+    """The 10,000-event 10 GeV calorimeter, every event recomputed by the
+    oracle (about 2 s on 16 cores), in the benchmark's launch configuration
+    (split schedule, CUDA graphs of 24 steps, 2^25 slots)."""
     s = W.calo_setup()
     n = 10000
     prim = W.calo_primaries(n)
-    hist, summ, st = gpu_run(emt, s, prim, n, slot_capacity=1 << 25, max_events=n)
-    led = np.abs(summ[:, 3] - summ[:, 0] - summ[:, 1] - summ[:, 2]) / summ[:, 3]
-    assert led.max() <= TOL
-    pick = np.random.default_rng(3).choice(n, 200, replace=False)
-    pick.sort()
-    sub = W.subset(prim, pick)
-    ohist, osumm = oracle_of(oracle_mod, s).run(sub, len(pick), pick.astype(np.uint64))
-    compare_events(summ[pick], osumm, hist[pick], ohist, frac=0.99)
+    hist, summ, st = gpu_run(emt, s, prim, n, slot_capacity=1 << 25, max_events=n, schedule="split",
+                             loop_mode="graph", graph_steps=24)
+    ohist, osumm = oracle_of(oracle_mod, s).run(prim, n, np.arange(n))
+    compare_events(summ, osumm, hist, ohist)
+    assert st["track_steps"] == int(osumm[:, 4].sum())
+
+
+def test_navigation_direction_below_fp32_range(emt, oracle_mod):
+    """Exits where a direction component is nonzero but below the FP32
+    normal range, so that its FP32 quotient estimate is 0/0 (a point exactly
+    on the wall) or infinite: photons without processes (no interaction,
+    straight) take one step, and every output field equals the oracle's."""
+    s = W.calo_setup(mask=0)
+    rec = np.array([
+        [0, 1000.0, 20.0, 0.0, 1.0, 1e-300, 0.0, 1.0, 3, 0],      # on the +x wall, ux tiny: exit at 0
+        [0, 1000.0, 3.0, -20.0, 1.0, 0.0, -1e-300, -1.0, 3, 0],   # on the -y wall, uy tiny, moving down
+        [0, 1000.0, 0.0, 0.0, 1e-37, 1.0, 0.0, -1e-38, 0, 0],     # z plane 10 cm away, x wall 20 cm
+        [0, 1000.0, 5.0, 20.0, 9.9, 0.0, 1e-310, 1.0, 28, 0],     # subnormal uy on the +y wall
+        [0, 1000.0, 0.0, 0.0, 9.9, 0.6, 0.0, 0.8, 28, 0],         # ordinary direction
+    ])
+    n = len(rec)
+    uid = np.arange(1, n + 1, dtype=np.uint64)
+    ctx = emt.context_for(s, slot_capacity=1 << 12, max_events=1)
+    empty = {"event": np.zeros(0, np.int32), "type": np.zeros(0, np.int32), "T": np.zeros(0),
+             "pos": np.zeros((0, 3)), "dir": np.zeros((0, 3))}
+    ctx.submit(np.array([5], np.uint64), empty)
+    ctx.debug_set_tracks(rec, uid, np.zeros(n, np.int32))
+    ctx.run(max_iterations=1)
+    grec, guid, _ = ctx.debug_get_tracks()
+    got = {int(u): r for u, r in zip(guid, grec)}
+    o = oracle_of(oracle_mod, s)
+    for i in range(n):
+        t, sec, info = o.step_one(rec[i], int(uid[i]), 5)
+        assert info[2] == 1 and len(sec) == 0
+        assert np.array_equal(got[int(uid[i])], t), (i, got[int(uid[i])], t)
+    assert got[1][8] == -1 and got[1][2] == 20.0   # left the stack on the spot
+    assert got[3][8] == -1 and got[3][4] == 0.0 and abs(got[3][2] - 10.0) < 1e-14  # z plane, not the x wall
+    ctx.debug_set_tracks(np.zeros((0, 10)), np.zeros(0, np.uint64), np.zeros(0, np.int32))
+    ctx.read_all()
+    ctx.close()
 
 
 def test_edge_cases(emt, oracle_mod):
