@@ -391,7 +391,8 @@ emt_status emt_debug_get_tracks(emt_ctx* ctx, int32_t cap, double* rec, uint64_t
  * as in emt_submit; hist[n_events][n_bins] and summary[n_events][6]:
  * caller-owned device buffers written in event order; cuda_stream: the
  * stream to run on (NULL: the legacy default stream).  Returns when the
- * results are complete.
+ * results are complete.  A primary whose type is not 0, 1 or 2 returns
+ * EMT_ERR_INVALID_ARG before any step runs (hist and summary unwritten).
  *
  * The first call on a device looks up the device address of the fixed
  * array (cudaGetSymbolAddress); make that first call before any stream

@@ -1492,15 +1492,21 @@ extern "C" emt_status emt_transport_static(int32_t device, uint32_t seed, const 
                                                              pl.max_events);
     if (cudaGetLastError() != cudaSuccess) return EMT_ERR_CUDA;
 
+    // ---- admission outcome: a primary of an unknown particle type is the
+    // caller's error, reported before any step runs
+    Counters h_cnt;
+    if (cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(&h_cnt, pool + pl.cnt, sizeof h_cnt, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return EMT_ERR_CUDA;
+    if (h_status & kStatusBadTrack) return EMT_ERR_INVALID_ARG;
+    if (h_status != 0) return EMT_ERR_CUDA;
+
     // ---- step loop (host-driven; one counter read per step)
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     const int block = 256;
     const int resident = std::max(1, sms * Launch<double>::max_blocks_per_sm(block));
-    Counters h_cnt;
-    if (cudaMemcpyAsync(&h_cnt, pool + pl.cnt, sizeof h_cnt, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
-        return EMT_ERR_CUDA;
     int64_t live_g = h_cnt.n[0], live_c = h_cnt.n[1];
     unsigned long long steps[2] = {0, 0}, last_steps = 0;
     for (int64_t it = 0; live_g + live_c > 0; ++it) {
