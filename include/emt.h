@@ -254,6 +254,8 @@ typedef struct emt_run_stats {
     int64_t held;         /* track copies held back by the track selection */
     int64_t spilled;      /* tracks moved to host memory by the host spill */
     int64_t peak_spilled; /* most tracks in host memory at once */
+    int64_t rk4_substeps; /* RK4 substeps of charged tracks in a field (each evaluation of the
+                             integrator, the repeat of a substep cut at a boundary included) */
 } emt_run_stats;
 
 /* Step every track in flight until none is left or max_iterations
@@ -346,6 +348,16 @@ typedef struct emt_serve_options {
 emt_status emt_serve(emt_ctx* ctx, int32_t n_events, const uint64_t* event_ids, const double* arrival_s,
                      const int32_t* first, const int32_t* count, const emt_primaries* prim,
                      const emt_serve_options* opt, double* admit_s, double* done_s, double* hist, double* summary);
+
+/* Measurement support (the paper has no counterpart): the FP64 fused
+ * multiply-add rate of device `device`, measured with independent DFMA
+ * chains over four full-occupancy waves of every SM, best of `repeats`
+ * launches of `iters` iterations (CUDA events); the denominator of the
+ * step kernels' FP64 roofline.  Allocates and frees a small buffer of its
+ * own.  host fma_per_s receives DFMA operations (one per thread) per
+ * second.  EMT_ERR_INVALID_ARG for non-positive counts, EMT_ERR_CUDA if
+ * the device cannot run it. */
+emt_status emt_measure_dfma_rate(int32_t device, int32_t iters, int32_t repeats, double* fma_per_s);
 
 /* Diagnostics: copy table (material m, particle p, quantity q) to host
  * out[n] (n = grid size).  gamma q: 0 photo, 1 compton, 2 pair;

@@ -25,6 +25,7 @@ UNITS = {
     "emt_kernels_fp64.cu": ["--fmad=false"],
     "emt_kernels_mixed.cu": [],
     "emt_serve.cu": [],
+    "emt_peak.cu": [],
 }
 
 

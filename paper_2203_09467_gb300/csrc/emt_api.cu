@@ -71,7 +71,7 @@ Plan make_plan(const emt_options& o)
         for (int f = 0; f < 11; ++f) p.trk[s][f] = p.add(Q * fs[f]);
     p.cnt = p.add(3 * sizeof(Counters));
     p.status = p.add(sizeof(int));
-    p.total_steps = p.add(3 * sizeof(unsigned long long));
+    p.total_steps = p.add(4 * sizeof(unsigned long long));
     p.done_head = p.add(sizeof(unsigned));
     p.ehist = p.add(3 * kEBins * sizeof(unsigned));
     const size_t E = (size_t)p.max_events;
@@ -247,7 +247,7 @@ struct emt_ctx {
     std::vector<int> order;  // slots in submission order
     unsigned done_seen = 0;
     // host mirrors valid while no device work has run since they were read
-    unsigned long long steps_seen[3] = {0, 0, 0};  // total step, deferred and held counters
+    unsigned long long steps_seen[4] = {0, 0, 0, 0};  // total step, deferred, held and RK4-substep counters
     unsigned head_cached = 0;                    // finished-event ring head
     bool head_fresh = false;
     // pinned host mirrors
@@ -489,7 +489,8 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
     std::memset(&s, 0, sizeof s);
     const Plan& pl = c->plan;
     c->head_fresh = false;
-    const unsigned long long steps0 = c->steps_seen[0], def0 = c->steps_seen[1], held0 = c->steps_seen[2];
+    const unsigned long long steps0 = c->steps_seen[0], def0 = c->steps_seen[1], held0 = c->steps_seen[2],
+                             sub0 = c->steps_seen[3];
     unsigned long long last_steps = steps0;
     const int64_t live0 = c->live_g + c->live_c;
     int64_t peak = live0;
@@ -659,6 +660,7 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
     c->steps_seen[0] = steps[0];
     c->steps_seen[1] = steps[1];
     c->steps_seen[2] = steps[2];
+    c->steps_seen[3] = steps[3];
     c->head_cached = *reinterpret_cast<const unsigned*>(c->h_misc + (pl.done_head - pl.status));
     c->head_fresh = true;
     if (status & (int)kStatusQueueOverflow) {
@@ -668,6 +670,7 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
     s.track_steps = (int64_t)(c->steps_seen[0] - steps0);
     s.deferred = (int64_t)(c->steps_seen[1] - def0);
     s.held = (int64_t)(c->steps_seen[2] - held0);
+    s.rk4_substeps = (int64_t)(c->steps_seen[3] - sub0);
     s.peak_tracks = peak;
     s.live_tracks = c->live_g + c->live_c + c->spill_n;
     s.kernel_ms = kernel_ms;
@@ -782,7 +785,7 @@ emt_status emt_create(const emt_options* o, emt_ctx** out)
     }
     if (cudaMallocHost((void**)&c->h_cnt, sizeof(Counters)) != cudaSuccess ||
         cudaMallocHost((void**)&c->h_status, sizeof(int)) != cudaSuccess ||
-        cudaMallocHost((void**)&c->h_steps, 3 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost((void**)&c->h_steps, 4 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost((void**)&c->h_done, sizeof(unsigned)) != cudaSuccess ||
         cudaMallocHost((void**)&c->h_misc, make_plan(*o).done_head + sizeof(unsigned) - make_plan(*o).status) !=
             cudaSuccess)

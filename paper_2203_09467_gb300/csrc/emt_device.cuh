@@ -199,7 +199,8 @@ struct Params {
     int* live;                      // [slot] tracks alive (+1 submission token)
     unsigned* done_ring;            // [max_events] slots of finished events
     unsigned* done_head;            // total finished events (ring index)
-    unsigned long long* total_steps;  // [0] track-steps taken, [1] deferred copies, [2] held copies
+    unsigned long long* total_steps;  // [0] track-steps taken, [1] deferred copies, [2] held copies,
+                                      // [3] RK4 substeps
     int max_events;
     uint32_t seed;
     // queues
@@ -330,7 +331,9 @@ struct Draws {
     __device__ __forceinline__ float u32(uint32_t j)
     {
         fill(j >> 2);
-        uint32_t v = w[j & 3u];
+        // a select chain keeps the words in registers (an indexed read
+        // would place w in local memory)
+        const uint32_t v = (j & 2u) ? ((j & 1u) ? w[3] : w[2]) : ((j & 1u) ? w[1] : w[0]);
         return __int_as_float((int)(0x3F800000u | (v >> 9))) - (1.0f - 0x1p-24f);
     }
 };
@@ -825,10 +828,10 @@ __device__ __forceinline__ bool chord_inside(const Params<R>& p, int vol, const 
 // n substeps of length hs (the caller derives both from h_max); the chord
 // of each substep is tested against the current volume and a crossing at
 // fraction f repeats the substep with h f, snapped onto the plane.
-// Returns the path length.
+// Returns the path length; *evals counts the integrator evaluations.
 template <int G, typename R>
 __device__ __forceinline__ double propagate_field(const Params<R>& p, int charge, double pm, int vol, double x[3],
-                                                  R u[3], int n, double hs, Exit* bnd, bool* crossed)
+                                                  R u[3], int n, double hs, Exit* bnd, bool* crossed, int* evals)
 {
     double kq = charge * kFieldC / pm;
     double s = 0.0;
@@ -837,6 +840,7 @@ __device__ __forceinline__ double propagate_field(const Params<R>& p, int charge
         double x1[3], c[3];
         R u1[3];
         rk4(p, R(kq), x, u, R(hs), x1, u1);
+        *evals += 1;
         if (!chord_inside<G>(p, vol, x, x1)) {
 #pragma unroll
             for (int a = 0; a < 3; ++a) c[a] = x1[a] - x[a];
@@ -844,6 +848,7 @@ __device__ __forceinline__ double propagate_field(const Params<R>& p, int charge
             if (e.t <= 1.0) {
                 double h2 = hs * e.t;
                 rk4(p, R(kq), x, u, R(h2), x1, u1);
+                *evals += 1;
                 if (e.axis >= 0) x1[e.axis] = e.plane;
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {

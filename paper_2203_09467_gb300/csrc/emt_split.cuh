@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(BS, transport_threads_per_sm<R>() / BS)
     __shared__ int s_chunk;
     __shared__ unsigned s_eh[S ? kEBins : 1];
     __shared__ Selection s_sel, s_spill;
+    __shared__ int s_cnt[kSubstepClasses], s_off[kSubstepClasses], s_perm[S ? 1 : BS];
     constexpr bool select = S;
     if (blockIdx.x == 0 && threadIdx.x == 0) p.cnt[cclr] = Counters{};
     if constexpr (select) {
@@ -86,10 +87,27 @@ __global__ void __launch_bounds__(BS, transport_threads_per_sm<R>() / BS)
         const int chunk = s_chunk;
         __syncthreads();
         if (chunk >= chunksG + chunksC) break;
-        const bool photon_chunk = chunk < chunksG;
-        const long long i = photon_chunk ? (long long)chunk * BS + tid : (long long)(chunk - chunksG) * BS + tid;
+        // In a field the charged chunks (tens of RK4 substeps per step) are
+        // handed out before the photon chunks, so that the cheap photon
+        // chunks fill the end of the launch instead of the expensive ones.
+        const bool charged_first = p.has_field != 0;
+        const bool photon_chunk = charged_first ? chunk >= chunksC : chunk < chunksG;
+        const int local = photon_chunk ? (charged_first ? chunk - chunksC : chunk)
+                                       : (charged_first ? chunk : chunk - chunksG);
+        long long i = (long long)local * BS + tid;
         const long long n_here = photon_chunk ? nG : nC;
         bool active = i < n_here;
+        if constexpr (!select) {
+            // charged tracks in a field: lanes of similar substep counts
+            // share a warp (the branch is uniform over the block)
+            if (p.has_field && !photon_chunk) {
+                const long long first = (long long)local * BS;
+                const long long in_chunk = n_here - first < BS ? n_here - first : BS;
+                const int j = regroup_by_substeps<R, BS>(p, qi, Q, nC, i, active, s_cnt, s_off, s_perm);
+                active = tid < in_chunk;
+                if (active) i = j;
+            }
+        }
         const long long src = photon_chunk ? i : Q - nC + i;
 
         TrackReg<R> t;
@@ -145,21 +163,24 @@ __global__ void __launch_bounds__(BS, transport_threads_per_sm<R>() / BS)
             const unsigned mh = __ballot_sync(0xFFFFFFFFu, held);
             if (lane == 0 && mh) atomicAdd(&p.total_steps[2], (unsigned long long)__popc(mh));
         }
+        int substeps = 0;
         if (held) {
             copy_out(t, o);
         } else if (active) {
             bool alive;
             model = transport_part<G, X>(p, t, fx, alive);
+            substeps = fx.substeps;
             if (model == kNoInteraction) {
                 finish_step(p, t, alive, fx, o);
                 apply_effects(p, t.ev, t.type, t.step, fx);
             }
         }
+        count_substeps(p, lane, substeps);
         {
             const unsigned ms = __ballot_sync(0xFFFFFFFFu, active && !held);
             if (lane == 0 && ms) atomicAdd(&p.total_steps[0], (unsigned long long)__popc(ms));
         }
-        emit(p, qo, co, lane, o, t.x, t.ev, t.vol, select ? s_eh : nullptr);
+        emit<1>(p, qo, co, lane, o, t.x, t.ev, t.vol, select ? s_eh : nullptr);
         // queue the interacting tracks
         const bool need = model != kNoInteraction;
         const unsigned m = __ballot_sync(0xFFFFFFFFu, need);
@@ -312,7 +333,7 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_interact(Params<R> p, int side
                 atomicAdd(&p.total_steps[1], (unsigned long long)__popc(md));
             }
         }
-        emit(p, qo, co, lane, o, t.x, t.ev, t.vol, select ? s_eh : nullptr);
+        emit<2>(p, qo, co, lane, o, t.x, t.ev, t.vol, select ? s_eh : nullptr);
         __syncthreads();
     }
     if constexpr (select) {

@@ -70,6 +70,7 @@ struct Effects {
     int col;      // histogram column of the deposits
     bool finished;
     int live_delta;
+    int substeps;  // RK4 evaluations of the step (field only)
 };
 
 // models, in the order of the cumulative selection per particle type
@@ -156,6 +157,7 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
     fx.kill = 0.0;
     fx.finished = false;
     fx.live_delta = 0;
+    fx.substeps = 0;
     const uint64_t event_id = p.event_id[t.ev];
     Draws dr;
     dr.init(p.seed, event_id, t.uid, t.step);
@@ -194,9 +196,24 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
     }
     const R kInf = R(__longlong_as_double(0x7FF0000000000000ll));
     R s_int = kInf;
+    int proc = nproc - 1;
     if (gt_zero(sig_tot)) {
         dr.next = 0;
         s_int = -mlog(draw<R>(dr)) / sig_tot;
+        // 9, taken early: the model by draw 1 (the same Philox block as
+        // draw 0) against the cumulative pre-step cross sections.  It reads
+        // only pre-step values, so it is the choice the step makes if it
+        // interacts (unused otherwise); taking it here frees the cross
+        // sections and the draw state before the propagation.
+        const R xsel = draw<R>(dr) * sig_tot;
+        R c = R(0);
+        for (int i = 0; i < nproc; ++i) {
+            c += sig[i];
+            if (lt_pos(xsel, c)) {
+                proc = i;
+                break;
+            }
+        }
     }
     R s_max = kInf;
     if (charged && matter) {
@@ -281,7 +298,7 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
             hs = smax / ns;
         }
         bool crossed = false;
-        s = propagate_field<G>(p, t.type == 1 ? -1 : 1, pm, t.vol, t.x, t.u, nsub, hs, &e, &crossed);
+        s = propagate_field<G>(p, t.type == 1 ? -1 : 1, pm, t.vol, t.x, t.u, nsub, hs, &e, &crossed, &fx.substeps);
         boundary = crossed;
     }
     if (boundary) interact = false;
@@ -316,18 +333,7 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
         return kNoInteraction;
     }
     if (!alive || !interact) return kNoInteraction;
-    // 9: model selection (draw 1) and closed channels
-    dr.next = 1;
-    R xsel = draw<R>(dr) * sig_tot;
-    int proc = nproc - 1;
-    R c = R(0);
-    for (int i = 0; i < nproc; ++i) {
-        c += sig[i];
-        if (lt_pos(xsel, c)) {
-            proc = i;
-            break;
-        }
-    }
+    // 9: the model chosen above, and channels closed at the post-loss energy
     const R T = t.T;
     if (t.type == 0) {
         if (proc == 0) return T > from_d<R>(p.bk[mi]) ? kPhoto : kNoInteraction;
@@ -399,25 +405,17 @@ __device__ __forceinline__ void interaction_part(const Params<R>& p, TrackReg<R>
     default: sample_annih(dr, T, t.u, pr); break;
     }
     if (pr.local != R(0)) fx.dep += to_d(pr.local);
-    int nsec = 0;
-    int sec_k[2];
-    int sec_type[2];
-    R sec_T[2];
-    R sec_u[2][3];
-    for (int k = 0; k < pr.n; ++k) {
-        int st = pr.type[k];
-        R sT = pr.T[k];
-        if (lt_pos(sT, pcut(p, st))) {
-            fx.dep += to_d(sT) + rest_energy(st);
-            continue;
+    // secondaries below their cut deposit on the spot (in the order k = 0, 1)
+    bool keep[2] = {false, false};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (k < pr.n) {
+            const int st = pr.type[k];
+            if (lt_pos(pr.T[k], pcut(p, st)))
+                fx.dep += to_d(pr.T[k]) + rest_energy(st);
+            else
+                keep[k] = true;
         }
-        sec_type[nsec] = st;
-        sec_T[nsec] = sT;
-        sec_u[nsec][0] = pr.dir[k][0];
-        sec_u[nsec][1] = pr.dir[k][1];
-        sec_u[nsec][2] = pr.dir[k][2];
-        sec_k[nsec] = k;
-        ++nsec;
     }
     bool alive = true;
     if (!pr.parent_alive) {
@@ -428,18 +426,127 @@ __device__ __forceinline__ void interaction_part(const Params<R>& p, TrackReg<R>
     }
     const uint32_t parent_step = t.step;
     finish_step(p, t, alive, fx, o);
-    for (int k = 0; k < nsec; ++k) {
-        int j = o.n;
-        o.type[j] = sec_type[k];
-        o.T[j] = sec_T[k];
-        o.u[j][0] = sec_u[k][0];
-        o.u[j][1] = sec_u[k][1];
-        o.u[j][2] = sec_u[k][2];
-        o.uid[j] = child_uid(p.seed, event_id, t.uid, parent_step, (uint32_t)sec_k[k]);
+    // outputs: the survivor (slot 0), then the kept secondaries in order.
+    // A surviving parent has at most one secondary, so every slot index
+    // below is a constant (the outputs stay in registers).
+    auto put = [&](int j, int k) {
+        o.type[j] = pr.type[k];
+        o.T[j] = pr.T[k];
+        o.u[j][0] = pr.dir[k][0];
+        o.u[j][1] = pr.dir[k][1];
+        o.u[j][2] = pr.dir[k][2];
+        o.uid[j] = child_uid(p.seed, event_id, t.uid, parent_step, (uint32_t)k);
         o.step[j] = 0;
-        o.n = j + 1;
+    };
+    if (o.n == 1) {
+        if (keep[0]) {
+            put(1, 0);
+            o.n = 2;
+        }
+    } else if (keep[0]) {
+        put(0, 0);
+        o.n = 1;
+        if (keep[1]) {
+            put(1, 1);
+            o.n = 2;
+        }
+    } else if (keep[1]) {
+        put(0, 1);
+        o.n = 1;
     }
-    fx.live_delta += nsec;
+    fx.live_delta += (int)keep[0] + (int)keep[1];
+}
+
+// Scheduling key of a charged track's next step in a field: an estimate,
+// in FP32, of its number of RK4 substeps, ceil(s / h_max) with s the
+// smallest of the free path (draw 0 of the step), the range limit and the
+// field-step limits, clamped to [1, kMaxSubsteps].  Boundaries are ignored
+// (an upper bound).  It only decides which lanes run together; the step
+// itself recomputes everything in the method's own arithmetic.
+template <typename R>
+__device__ __forceinline__ int field_substeps_estimate(const Params<R>& p, const TrackReg<R>& t)
+{
+    const float T = est_f(t.T);
+    const float pm = sqrtf(T * (T + 2.0f * (float)kMe));
+    const float hmax = sqrtf(8.0f * (pm / ((float)kFieldC * (float)p.bmag)) * (float)p.rk_delta);
+    float s = fminf((float)p.max_field_step, (float)kMaxSubsteps * hmax);
+    const int mi = t.vol >= 0 ? p.lmat[t.vol] : -1;
+    if (mi >= 0 && !p.vacuum[mi]) {
+        const size_t row = (size_t)(mi * 3 + t.type) * p.n_grid * kNq;
+        const R* tab = p.tab + row;
+        const R* dtab = p.dtab + row;
+        const Lookup<R> lk = locate_energy(p, t.T);
+        const float rng = est_f(range_value(p, tab, dtab, t.T, lk));
+        const float lim = fminf(rng, est_f(pfinal_range(p)));
+        s = fminf(s, fmaxf(est_f(pstep_frac(p)) * rng, lim));
+        float sig = est_f(xs_value(p, tab, dtab, lk, 0)) + est_f(xs_value(p, tab, dtab, lk, 1));
+        if (t.type == 2) sig += est_f(xs_value(p, tab, dtab, lk, 2));
+        if (sig > 0.0f) {
+            Draws dr;
+            dr.init(p.seed, p.event_id[t.ev], t.uid, t.step);
+            dr.fill(0);
+            const float u = __uint_as_float(0x3F800000u | (dr.w[1] >> 9)) - (1.0f - 0x1p-24f);
+            s = fminf(s, -__logf(u) / sig);
+        }
+    }
+    const float n = ceilf(s / hmax);
+    return n < 1.0f ? 1 : (n > (float)kMaxSubsteps ? kMaxSubsteps : (int)n);
+}
+
+// Regroup a chunk of charged tracks in a field so that lanes with similar
+// substep counts share a warp: each thread estimates the substep count of
+// the track at input index i (active lanes only), the block counting-sorts
+// the chunk by it (descending, 32 classes of 4 substeps) and every thread
+// takes the index at its rank.  The warps of the chunk then run near-equal
+// numbers of RK4 iterations instead of the maximum over a random mix.
+// Inactive lanes (past the end of the input) sort last.  Every thread of
+// the block calls it (it has barriers).
+constexpr int kSubstepClasses = 32;
+
+template <typename R, int BS>
+__device__ __forceinline__ long long regroup_by_substeps(const Params<R>& p, const Tracks<R>& qi, long long Q,
+                                                         int nC, long long i, bool active, int* cnt, int* off,
+                                                         int* perm)
+{
+    const int tid = threadIdx.x;
+    int key = -1;
+    if (active) {
+        TrackReg<R> t;
+        load_track(qi, Q - nC + i, t);
+        const int n = field_substeps_estimate(p, t);
+        key = (n - 1) >> 2;  // 0 .. 24
+    }
+    if (tid < kSubstepClasses) cnt[tid] = 0;
+    __syncthreads();
+    int rank = 0;
+    if (key >= 0) rank = atomicAdd(&cnt[key], 1);
+    __syncthreads();
+    if (tid < 32) {
+        // descending classes: offset of class k = tracks in classes > k
+        const int k = kSubstepClasses - 1 - tid;
+        const int c = cnt[k];
+        int incl = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+            if (tid >= d) incl += y;
+        }
+        off[k] = incl - c;
+    }
+    __syncthreads();
+    if (key >= 0) perm[off[key] + rank] = (int)i;
+    __syncthreads();
+    return perm[tid];  // valid for tid < the chunk's active count
+}
+
+// RK4 evaluations of a warp's steps into the run's counter (field only;
+// every lane of the warp calls it)
+template <typename R>
+__device__ __forceinline__ void count_substeps(const Params<R>& p, int lane, int substeps)
+{
+    if (!p.has_field) return;
+    const unsigned v = __reduce_add_sync(0xFFFFFFFFu, (unsigned)substeps);
+    if (lane == 0 && v) atomicAdd(&p.total_steps[3], (unsigned long long)v);
 }
 
 template <typename R>
@@ -493,18 +600,23 @@ __device__ __forceinline__ void copy_out(const TrackReg<R>& t, StepOut<R>& o)
 // warp-aggregated reservation and store of each lane's outputs (all lanes
 // of the warp call it); counts are packed as photons | charged << 16.
 // With track selection on, eh (shared memory) counts the outputs' energy
-// classes.
-template <typename R>
+// classes.  kMaxOut: the most outputs a lane can have (1 after the
+// transport part, 2 after an interaction); the loops over the outputs are
+// unrolled to it, so the outputs stay in registers.
+template <int kMaxOut, typename R>
 __device__ __forceinline__ void emit(const Params<R>& p, const Tracks<R>& qo, Counters* cout, int lane,
                                      const StepOut<R>& o, const double x[3], uint32_t ev, int vol,
                                      unsigned* eh = nullptr)
 {
     int ng = 0, nc = 0;
-    for (int k = 0; k < o.n; ++k) {
-        if (o.type[k] == 0)
-            ++ng;
-        else
-            ++nc;
+#pragma unroll
+    for (int k = 0; k < kMaxOut; ++k) {
+        if (k < o.n) {
+            if (o.type[k] == 0)
+                ++ng;
+            else
+                ++nc;
+        }
     }
     const int v = ng | (nc << 16);
     int incl = v;
@@ -527,7 +639,9 @@ __device__ __forceinline__ void emit(const Params<R>& p, const Tracks<R>& qo, Co
     long long og = (long long)baseG + (excl & 0xFFFF);
     long long oc = (long long)baseC + (excl >> 16);
     const long long Q = p.Q;
-    for (int k = 0; k < o.n; ++k) {
+#pragma unroll
+    for (int k = 0; k < kMaxOut; ++k) {
+        if (k >= o.n) break;
         long long dst;
         if (o.type[k] == 0) {
             dst = og++;
@@ -667,10 +781,12 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_step(Params<R> p, int side, in
         o.n = 0;
         int model = kNoInteraction;
         int rank = 0;
+        int substeps = 0;
         if (active) {
             load_track(qi, src, t);
             bool alive;
             model = transport_part<G, X>(p, t, fx, alive);
+            substeps = fx.substeps;
             if (model == kNoInteraction) {
                 finish_step(p, t, alive, fx, o);
                 apply_effects(p, t.ev, t.type, t.step, fx);
@@ -678,11 +794,12 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_step(Params<R> p, int side, in
                 rank = atomicAdd(&sg.count[model], 1);
             }
         }
+        count_substeps(p, lane, substeps);
         {
             const unsigned ms = __ballot_sync(0xFFFFFFFFu, active);
             if (lane == 0 && ms) atomicAdd(&p.total_steps[0], (unsigned long long)__popc(ms));
         }
-        emit(p, qo, co, lane, o, t.x, t.ev, t.vol);
+        emit<1>(p, qo, co, lane, o, t.x, t.ev, t.vol);
         __syncthreads();
         if (tid == 0) {
             int acc = 0;
@@ -771,7 +888,7 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_step(Params<R> p, int side, in
                 atomicAdd(&p.total_steps[1], (unsigned long long)__popc(md));
             }
         }
-        emit(p, qo, co, lane, o, t.x, t.ev, t.vol);
+        emit<2>(p, qo, co, lane, o, t.x, t.ev, t.vol);
         __syncthreads();
     }
 }

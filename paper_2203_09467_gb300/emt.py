@@ -86,7 +86,7 @@ class RunStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int64), ("track_steps", ctypes.c_int64), ("peak_tracks", ctypes.c_int64),
                 ("deferred", ctypes.c_int64), ("live_tracks", ctypes.c_int64), ("state_bytes", ctypes.c_int64),
                 ("kernel_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int32), ("held", ctypes.c_int64),
-                ("spilled", ctypes.c_int64), ("peak_spilled", ctypes.c_int64)]
+                ("spilled", ctypes.c_int64), ("peak_spilled", ctypes.c_int64), ("rk4_substeps", ctypes.c_int64)]
 
 
 _lib = None
@@ -124,6 +124,8 @@ _SIGS = {
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(Primaries),
                                    ctypes.POINTER(ServeOptions), ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p]),
+    "emt_measure_dfma_rate": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                               ctypes.POINTER(ctypes.c_double)]),
     "emt_transport_static": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_uint32, ctypes.POINTER(Material),
                                               ctypes.c_int32, ctypes.POINTER(Physics), ctypes.POINTER(Layer),
                                               ctypes.c_int32, ctypes.POINTER(World), ctypes.c_int32,
@@ -413,6 +415,15 @@ class Context:
         self._check(lib().emt_debug_get_tracks(self._h, cap, _ptr(rec), _ptr(uid), _ptr(sl), ctypes.byref(n)))
         k = n.value
         return rec[:k].copy(), uid[:k].copy(), sl[:k].copy()
+
+
+def measure_dfma_rate(device: int = 0, iters: int = 4000, repeats: int = 5) -> float:
+    """FP64 fused multiply-adds per second of the device (emt_measure_dfma_rate)."""
+    out = ctypes.c_double()
+    rc = lib().emt_measure_dfma_rate(int(device), int(iters), int(repeats), ctypes.byref(out))
+    if rc != 0:
+        raise EmtError(rc, "emt_measure_dfma_rate failed")
+    return out.value
 
 
 def context_for(setup, **kw) -> Context:
