@@ -45,6 +45,7 @@ struct Plan {
     size_t st_ev, st_type, st_T, st_pos, st_dir, st_uid, st_slot, st_ids, st_start, st_runs;
     size_t slots_tmp, out_hist, out_summary;
     size_t iq[13];  // split schedule: interaction queue fields
+    size_t skey, sperm;  // split schedule: scheduling classes and order of charged tracks in a field
     size_t step_hist;  // [3][step_bins] when step_bins > 0
     int step_bins;
     size_t spill[11];     // host spill: staging buffer of Q track records (when spill_above > 0)
@@ -120,8 +121,11 @@ Plan make_plan(const emt_options& o)
         // x y z ux uy uz T uid dep ev step tv src
         const size_t iqs[13] = {8, 8, 8, rs, rs, rs, rs, 8, 8, 4, 4, 4, 4};
         for (int f = 0; f < 13; ++f) p.iq[f] = p.add(Q * iqs[f]);
+        p.skey = p.add(Q);
+        p.sperm = p.add(Q * 4);
     } else {
         for (int f = 0; f < 13; ++f) p.iq[f] = 0;
+        p.skey = p.sperm = 0;
     }
     p.out_hist = p.add(E * (size_t)o.max_bins * sizeof(double));
     p.out_summary = p.add(E * EMT_SUMMARY_LEN * sizeof(double));
@@ -338,6 +342,8 @@ void fill_common(emt_ctx* c, Params<R>& p)
         q.step = c->at<uint32_t>(pl.iq[10]);
         q.tv = c->at<uint32_t>(pl.iq[11]);
         q.src = c->at<uint32_t>(pl.iq[12]);
+        p.skey = c->at<uint8_t>(pl.skey);
+        p.sperm = c->at<uint32_t>(pl.sperm);
     }
     p.Q = pl.Q;
     p.cnt = c->at<Counters>(pl.cnt);

@@ -119,6 +119,11 @@ struct Tracks {
     uint32_t* tv;    // type (bits 0-7) | (volume + 2) << 8
 };
 
+// scheduling classes of charged tracks in a field (split schedule): class
+// c holds the tracks whose estimated RK4 substep count n satisfies
+// (kMaxSubsteps - n) >> 2 == c, so class 0 is the most expensive
+constexpr int kSortKeys = 32;
+
 // per-iteration counters, rotating over three slots (input, output, clear)
 struct Counters {
     int n[2];      // photons, charged
@@ -128,6 +133,8 @@ struct Counters {
     int work_b;    // split schedule: chunk dispenser of the interaction kernel
     int ticket;    // track selection: tickets of the boundary energy class
     int spilled;   // host spill: tracks written to the spill buffer
+    int kbin[kSortKeys];  // field: charged input tracks per scheduling class
+    int kcur[kSortKeys];  // field: places taken per class while the order is written
 };
 
 // Split schedule: tracks that interact in a step, queued by the transport
@@ -209,6 +216,12 @@ struct Params {
     Counters* cnt;  // [3]
     int* status;
     InterQueue<R> iq;  // split schedule only
+    // split schedule in a field: scheduling class of each charged input
+    // track (skey[i], i = index in the charged region) and the order in
+    // which the transport kernel takes them (sperm: indices, most
+    // expensive class first); Q entries each
+    uint8_t* skey;
+    uint32_t* sperm;
     // track selection: at most max_active tracks step per iteration (0 =
     // all), chosen by select_policy; the others are held (copied
     // unchanged).  ehist[3][kEBins]: energy classes of each counter slot's

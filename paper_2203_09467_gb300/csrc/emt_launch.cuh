@@ -117,6 +117,12 @@ template <typename R, int BS, bool S, bool X>
 static void launch_split_x(const Params<R>& p, int side, int cin, int cout, int cclr, int grid_a, int grid_b,
                            cudaStream_t st)
 {
+    if (!S && p.has_field) {
+        // charged tracks sorted by expected substep count (k_transport takes
+        // them in that order)
+        k_sort_keys<R><<<grid_b, 256, 0, st>>>(p, side, cin);
+        k_sort_order<R><<<grid_b, 256, 0, st>>>(p, cin);
+    }
     if (p.geom == kGeomCylinders)
         k_transport<R, BS, kGeomCylinders, S, X><<<grid_a, BS, 0, st>>>(p, side, cin, cout, cclr);
     else

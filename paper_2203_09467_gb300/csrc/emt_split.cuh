@@ -37,6 +37,139 @@ constexpr int transport_threads_per_sm()
     return sizeof(R) == 8 ? 768 : 640;
 }
 
+// Phase A of one track in the transport kernel (every lane of the warp
+// calls it; `active` lanes hold a track in t, `held` ones are copied
+// unchanged): transport, survivor output, and the queueing of an
+// interacting track for the interaction kernel.
+template <int G, bool X, typename R>
+__device__ __forceinline__ void transport_lane(const Params<R>& p, const Tracks<R>& qo, Counters* co, int cin,
+                                               int lane, TrackReg<R>& t, bool active, bool held, long long src,
+                                               unsigned* eh)
+{
+    const unsigned lanes_below = (1u << lane) - 1u;
+    Effects fx;
+    StepOut<R> o;
+    o.n = 0;
+    int model = kNoInteraction;
+    int substeps = 0;
+    if (held) {
+        copy_out(t, o);
+    } else if (active) {
+        bool alive;
+        model = transport_part<G, X>(p, t, fx, alive);
+        substeps = fx.substeps;
+        if (model == kNoInteraction) {
+            finish_step(p, t, alive, fx, o);
+            apply_effects(p, t.ev, t.type, t.step, fx);
+        }
+    }
+    count_substeps(p, lane, substeps);
+    {
+        const unsigned ms = __ballot_sync(0xFFFFFFFFu, active && !held);
+        if (lane == 0 && ms) atomicAdd(&p.total_steps[0], (unsigned long long)__popc(ms));
+    }
+    emit<1>(p, qo, co, lane, o, t.x, t.ev, t.vol, eh);
+    // queue the interacting tracks
+    const bool need = model != kNoInteraction;
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, need);
+    if (m) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&p.cnt[cin].n_int, __popc(m));
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (need) {
+            const long long k = (long long)base + __popc(m & lanes_below);
+            const InterQueue<R>& iq = p.iq;
+            if (k < p.Q) {
+                iq.x[k] = t.x[0];
+                iq.y[k] = t.x[1];
+                iq.z[k] = t.x[2];
+                iq.ux[k] = t.u[0];
+                iq.uy[k] = t.u[1];
+                iq.uz[k] = t.u[2];
+                iq.T[k] = t.T;
+                iq.uid[k] = t.uid;
+                iq.dep[k] = fx.dep;
+                iq.ev[k] = t.ev;
+                iq.step[k] = t.step;
+                iq.tv[k] = pack_tvm(t.type, t.vol, model);
+                iq.src[k] = (uint32_t)src;
+            } else {
+                atomicOr(p.status, kStatusQueueOverflow);
+            }
+        }
+    }
+}
+
+// The charged tracks of a step in a field, sorted by expected cost (a
+// counting sort by scheduling class, two launches before the transport
+// kernel): k_sort_keys estimates each track's RK4 substep count and counts
+// the classes; k_sort_order writes the order, most expensive class first.
+// The transport kernel then takes the charged tracks in that order, a warp
+// at a time: warps run lanes of similar substep counts (instead of a random
+// mix, whose slowest lane sets the warp's time), the expensive warps start
+// first and the cheap ones fill the end of the launch.  The order within a
+// class is arbitrary; results do not depend on it.
+template <typename R>
+__global__ void __launch_bounds__(256) k_sort_keys(Params<R> p, int side, int cin)
+{
+    __shared__ int h[kSortKeys];
+    if (threadIdx.x < kSortKeys) h[threadIdx.x] = 0;
+    __syncthreads();
+    const int nC = p.cnt[cin].n[1];
+    const Tracks<R> qi = p.q[side];
+    const long long base = p.Q - nC;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nC;
+         i += (long long)gridDim.x * blockDim.x) {
+        TrackReg<R> t;
+        t.T = qi.T[base + i];
+        t.uid = qi.uid[base + i];
+        t.ev = qi.ev[base + i];
+        t.step = qi.step[base + i];
+        const uint32_t tv = qi.tv[base + i];
+        t.type = tv_type(tv);
+        t.vol = tv_vol(tv);
+        const int cls = (kMaxSubsteps - field_substeps_estimate(p, t)) >> 2;
+        p.skey[i] = (uint8_t)cls;
+        atomicAdd(&h[cls], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < kSortKeys && h[threadIdx.x]) atomicAdd(&p.cnt[cin].kbin[threadIdx.x], h[threadIdx.x]);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_sort_order(Params<R> p, int cin)
+{
+    __shared__ int off[kSortKeys], cnt[kSortKeys], base[kSortKeys];
+    const int tid = threadIdx.x;
+    const int nC = p.cnt[cin].n[1];
+    if (tid < 32) {
+        // first place of each class: exclusive prefix sum of the counts
+        const int c = tid < kSortKeys ? p.cnt[cin].kbin[tid] : 0;
+        int incl = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+            if (tid >= d) incl += y;
+        }
+        if (tid < kSortKeys) off[tid] = incl - c;
+    }
+    for (long long first = (long long)blockIdx.x * blockDim.x; first < nC; first += (long long)gridDim.x * blockDim.x) {
+        if (tid < kSortKeys) cnt[tid] = 0;
+        __syncthreads();
+        const long long i = first + tid;
+        int key = -1, rank = 0;
+        if (i < nC) {
+            key = p.skey[i];
+            rank = atomicAdd(&cnt[key], 1);
+        }
+        __syncthreads();
+        if (tid < kSortKeys && cnt[tid]) base[tid] = atomicAdd(&p.cnt[cin].kcur[tid], cnt[tid]);
+        __syncthreads();
+        if (key >= 0) p.sperm[off[key] + base[key] + rank] = (uint32_t)i;
+        __syncthreads();
+    }
+}
+
 template <typename R, int BS, int G, bool S, bool X>
 __global__ void __launch_bounds__(BS, transport_threads_per_sm<R>() / BS)
     k_transport(Params<R> p, int side, int cin, int cout, int cclr)
@@ -44,9 +177,50 @@ __global__ void __launch_bounds__(BS, transport_threads_per_sm<R>() / BS)
     __shared__ int s_chunk;
     __shared__ unsigned s_eh[S ? kEBins : 1];
     __shared__ Selection s_sel, s_spill;
-    __shared__ int s_cnt[kSubstepClasses], s_off[kSubstepClasses], s_perm[S ? 1 : BS];
     constexpr bool select = S;
     if (blockIdx.x == 0 && threadIdx.x == 0) p.cnt[cclr] = Counters{};
+    const Tracks<R> qi = p.q[side];
+    const Tracks<R> qo = p.q[side ^ 1];
+    const int nG = p.cnt[cin].n[0];
+    const int nC = p.cnt[cin].n[1];
+    const long long Q = p.Q;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const unsigned lanes_below = (1u << lane) - 1u;
+    Counters* const co = &p.cnt[cout];
+    // In a field the charged tracks (tens of RK4 substeps per step) are
+    // handed out before the photons, so that the cheap photon work fills
+    // the end of the launch instead of the expensive charged work.
+    const bool charged_first = p.has_field != 0;
+
+    if constexpr (!select) {
+        // Chunks of one warp, taken by each warp on its own (no block
+        // barrier: a warp never waits for the slowest warp of its block).
+        // In a field the charged tracks are taken in the order of
+        // k_sort_order (most expensive first).
+        const int chunksG = (nG + 31) >> 5;
+        const int chunksC = (nC + 31) >> 5;
+        const bool sorted = p.has_field != 0;
+        for (;;) {
+            int chunk = 0;
+            if (lane == 0) chunk = atomicAdd(&p.cnt[cin].work, 1);
+            chunk = __shfl_sync(0xFFFFFFFFu, chunk, 0);
+            if (chunk >= chunksG + chunksC) break;
+            const bool photon_chunk = charged_first ? chunk >= chunksC : chunk < chunksG;
+            const int local = photon_chunk ? (charged_first ? chunk - chunksC : chunk)
+                                           : (charged_first ? chunk : chunk - chunksG);
+            long long i = (long long)local * 32 + lane;
+            const bool active = i < (photon_chunk ? nG : nC);
+            if (sorted && !photon_chunk && active) i = p.sperm[i];
+            const long long src = photon_chunk ? i : Q - nC + i;
+            TrackReg<R> t;
+            if (active) load_track(qi, src, t);
+            transport_lane<G, X>(p, qo, co, cin, lane, t, active, false, src, nullptr);
+        }
+        return;
+    }
+
+    // track selection: chunks of a block (the selection is block-wide)
     if constexpr (select) {
         for (int b = threadIdx.x; b < kEBins; b += BS) {
             s_eh[b] = 0u;
@@ -68,53 +242,23 @@ __global__ void __launch_bounds__(BS, transport_threads_per_sm<R>() / BS)
         }
         __syncthreads();
     }
-    const Tracks<R> qi = p.q[side];
-    const Tracks<R> qo = p.q[side ^ 1];
-    const int nG = p.cnt[cin].n[0];
-    const int nC = p.cnt[cin].n[1];
-    const long long Q = p.Q;
     const int chunksG = (nG + BS - 1) / BS;
     const int chunksC = (nC + BS - 1) / BS;
-    const int tid = threadIdx.x;
-    const int lane = tid & 31;
-    const unsigned lanes_below = (1u << lane) - 1u;
-    Counters* const co = &p.cnt[cout];
-    const InterQueue<R> iq = p.iq;
-
     for (;;) {
         if (tid == 0) s_chunk = atomicAdd(&p.cnt[cin].work, 1);
         __syncthreads();
         const int chunk = s_chunk;
         __syncthreads();
         if (chunk >= chunksG + chunksC) break;
-        // In a field the charged chunks (tens of RK4 substeps per step) are
-        // handed out before the photon chunks, so that the cheap photon
-        // chunks fill the end of the launch instead of the expensive ones.
-        const bool charged_first = p.has_field != 0;
         const bool photon_chunk = charged_first ? chunk >= chunksC : chunk < chunksG;
         const int local = photon_chunk ? (charged_first ? chunk - chunksC : chunk)
                                        : (charged_first ? chunk : chunk - chunksG);
-        long long i = (long long)local * BS + tid;
+        const long long i = (long long)local * BS + tid;
         const long long n_here = photon_chunk ? nG : nC;
         bool active = i < n_here;
-        if constexpr (!select) {
-            // charged tracks in a field: lanes of similar substep counts
-            // share a warp (the branch is uniform over the block)
-            if (p.has_field && !photon_chunk) {
-                const long long first = (long long)local * BS;
-                const long long in_chunk = n_here - first < BS ? n_here - first : BS;
-                const int j = regroup_by_substeps<R, BS>(p, qi, Q, nC, i, active, s_cnt, s_off, s_perm);
-                active = tid < in_chunk;
-                if (active) i = j;
-            }
-        }
         const long long src = photon_chunk ? i : Q - nC + i;
 
         TrackReg<R> t;
-        Effects fx;
-        StepOut<R> o;
-        o.n = 0;
-        int model = kNoInteraction;
         bool held = false;
         if (active) load_track(qi, src, t);
         if constexpr (select) {
@@ -163,52 +307,7 @@ __global__ void __launch_bounds__(BS, transport_threads_per_sm<R>() / BS)
             const unsigned mh = __ballot_sync(0xFFFFFFFFu, held);
             if (lane == 0 && mh) atomicAdd(&p.total_steps[2], (unsigned long long)__popc(mh));
         }
-        int substeps = 0;
-        if (held) {
-            copy_out(t, o);
-        } else if (active) {
-            bool alive;
-            model = transport_part<G, X>(p, t, fx, alive);
-            substeps = fx.substeps;
-            if (model == kNoInteraction) {
-                finish_step(p, t, alive, fx, o);
-                apply_effects(p, t.ev, t.type, t.step, fx);
-            }
-        }
-        count_substeps(p, lane, substeps);
-        {
-            const unsigned ms = __ballot_sync(0xFFFFFFFFu, active && !held);
-            if (lane == 0 && ms) atomicAdd(&p.total_steps[0], (unsigned long long)__popc(ms));
-        }
-        emit<1>(p, qo, co, lane, o, t.x, t.ev, t.vol, select ? s_eh : nullptr);
-        // queue the interacting tracks
-        const bool need = model != kNoInteraction;
-        const unsigned m = __ballot_sync(0xFFFFFFFFu, need);
-        if (m) {
-            int base = 0;
-            if (lane == 0) base = atomicAdd(&p.cnt[cin].n_int, __popc(m));
-            base = __shfl_sync(0xFFFFFFFFu, base, 0);
-            if (need) {
-                const long long k = (long long)base + __popc(m & lanes_below);
-                if (k < Q) {
-                    iq.x[k] = t.x[0];
-                    iq.y[k] = t.x[1];
-                    iq.z[k] = t.x[2];
-                    iq.ux[k] = t.u[0];
-                    iq.uy[k] = t.u[1];
-                    iq.uz[k] = t.u[2];
-                    iq.T[k] = t.T;
-                    iq.uid[k] = t.uid;
-                    iq.dep[k] = fx.dep;
-                    iq.ev[k] = t.ev;
-                    iq.step[k] = t.step;
-                    iq.tv[k] = pack_tvm(t.type, t.vol, model);
-                    iq.src[k] = (uint32_t)src;
-                } else {
-                    atomicOr(p.status, kStatusQueueOverflow);
-                }
-            }
-        }
+        transport_lane<G, X>(p, qo, co, cin, lane, t, active, held, src, s_eh);
     }
     if constexpr (select) {
         __syncthreads();

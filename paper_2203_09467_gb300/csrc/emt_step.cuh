@@ -493,52 +493,6 @@ __device__ __forceinline__ int field_substeps_estimate(const Params<R>& p, const
     return n < 1.0f ? 1 : (n > (float)kMaxSubsteps ? kMaxSubsteps : (int)n);
 }
 
-// Regroup a chunk of charged tracks in a field so that lanes with similar
-// substep counts share a warp: each thread estimates the substep count of
-// the track at input index i (active lanes only), the block counting-sorts
-// the chunk by it (descending, 32 classes of 4 substeps) and every thread
-// takes the index at its rank.  The warps of the chunk then run near-equal
-// numbers of RK4 iterations instead of the maximum over a random mix.
-// Inactive lanes (past the end of the input) sort last.  Every thread of
-// the block calls it (it has barriers).
-constexpr int kSubstepClasses = 32;
-
-template <typename R, int BS>
-__device__ __forceinline__ long long regroup_by_substeps(const Params<R>& p, const Tracks<R>& qi, long long Q,
-                                                         int nC, long long i, bool active, int* cnt, int* off,
-                                                         int* perm)
-{
-    const int tid = threadIdx.x;
-    int key = -1;
-    if (active) {
-        TrackReg<R> t;
-        load_track(qi, Q - nC + i, t);
-        const int n = field_substeps_estimate(p, t);
-        key = (n - 1) >> 2;  // 0 .. 24
-    }
-    if (tid < kSubstepClasses) cnt[tid] = 0;
-    __syncthreads();
-    int rank = 0;
-    if (key >= 0) rank = atomicAdd(&cnt[key], 1);
-    __syncthreads();
-    if (tid < 32) {
-        // descending classes: offset of class k = tracks in classes > k
-        const int k = kSubstepClasses - 1 - tid;
-        const int c = cnt[k];
-        int incl = c;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-            if (tid >= d) incl += y;
-        }
-        off[k] = incl - c;
-    }
-    __syncthreads();
-    if (key >= 0) perm[off[key] + rank] = (int)i;
-    __syncthreads();
-    return perm[tid];  // valid for tid < the chunk's active count
-}
-
 // RK4 evaluations of a warp's steps into the run's counter (field only;
 // every lane of the warp calls it)
 template <typename R>
