@@ -487,6 +487,16 @@ emt_status sync_status(emt_ctx* c, const char* where)
     return EMT_OK;
 }
 
+// kernel launches of one step: the fused kernel; or the transport and
+// interaction kernels, plus the two sorting launches of the charged tracks
+// in a field (without track selection)
+template <typename R>
+int launches_per_step(const emt_ctx* c, const Params<R>& p)
+{
+    if (!c->plan.split) return 1;
+    return 2 + ((p.has_field && p.max_active <= 0) ? 2 : 0);
+}
+
 template <typename R>
 emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
 {
@@ -587,7 +597,7 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
                 : Launch<R>::step(p, side, cin, cout, cclr, grid, c->block, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
         EMT_CUDA(c, cudaEventRecord(c->ev1, c->stream));
-        s.kernel_launches += c->plan.split ? 2 : 1;
+        s.kernel_launches += launches_per_step(c, p);
         c->it += 1;
         s.iterations += 1;
         const int64_t g0 = c->live_g, c0 = c->live_c;
@@ -649,7 +659,7 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
             EMT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
             EMT_CUDA(c, cudaGraphLaunch(c->graph, c->stream));
             EMT_CUDA(c, cudaEventRecord(c->ev1, c->stream));
-            s.kernel_launches += c->plan.split ? 2 * K : K;
+            s.kernel_launches += K * launches_per_step(c, p);
             c->it += K;
             s.iterations += K;
             done_it += K;
