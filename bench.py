@@ -15,9 +15,12 @@ read every event's scores.  Default workload: the sampling calorimeter
   cpu_baseline : the FP64 CPU oracle on the host cores, on a bounded sample
           of the same workload
 
-Under torchrun each rank runs its own shard of events (weak scaling: the
-per-GPU workload is fixed); there is no collective on the data path.
-`--impl reference` times the CPU oracle instead (rank 0 only).
+Under torchrun with N ranks the workload is one set of N x events events,
+partitioned across the ranks by cost (greedy on the primaries' energy,
+paper_2203_09467_gb300.shard): each rank transports its shard with no
+exchange while stepping (weak scaling: the per-GPU work stays fixed), and
+the per-event results are gathered once, in event order, after the timed
+steps.  `--impl reference` times the CPU oracle instead (rank 0 only).
 """
 from __future__ import annotations
 
@@ -76,11 +79,11 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def workload(name, n_events, rank):
-    """Setup, primaries and event ids of this rank's shard."""
+def workload(name, n_events):
+    """Setup, primaries and event ids of the whole workload."""
     if name == "calo":
         s = W.calo_setup()
-        prim = W.calo_primaries(n_events, seed=s.seed + 7919 * rank)
+        prim = W.calo_primaries(n_events, seed=s.seed)
         desc = f"sampling calorimeter 50x(2mm Pb+5mm LAr), {n_events} events x 10 GeV e-"
     elif name == "slab":
         s = W.slab_setup()
@@ -88,26 +91,26 @@ def workload(name, n_events, rank):
         desc = f"5 cm Pb slab, {n_events} events x 100 MeV e-"
     elif name == "calo_field":
         s = W.calo_field_setup()
-        prim = W.calo_field_primaries(n_events, seed=s.seed + 7919 * rank)
+        prim = W.calo_field_primaries(n_events, seed=s.seed)
         desc = f"calorimeter in 2 T field, {n_events} events, e-/e+/gamma 1-100 GeV"
     elif name == "batched":
         s = W.calo_field_setup()
         s.seed = 4
-        prim = W.batched_primaries(n_events, seed=4 + 7919 * rank)
+        prim = W.batched_primaries(n_events, seed=4)
         desc = f"calorimeter in 2 T field, {n_events} events of 1-64 primaries, 0.1-100 GeV"
     elif name == "served":
         s = W.calo_field_setup()
         s.seed = 5
-        prim = W.served_primaries(n_events, seed=5 + 7919 * rank)
+        prim = W.served_primaries(n_events, seed=5)
         desc = f"calorimeter in 2 T field, {n_events} requests of 1-100 primaries, 1-50 GeV"
     elif name in ("cms", "cms_field"):
         s = W.cms_setup() if name == "cms" else W.cms_field_setup()
-        prim = W.cms_primaries(n_events, 1000, seed=s.seed + 7919 * rank)
+        prim = W.cms_primaries(n_events, 1000, seed=s.seed)
         desc = (f"CMS-like 6 cylindrical shells to 375 cm (vacuum, Si, Pb, C, Ti, Fe)"
                 f"{', 3.8 T along z' if name == 'cms_field' else ''}, {n_events} events x 1000 isotropic 1 GeV photons")
     else:
         raise SystemExit(f"unknown workload {name}")
-    ids = (np.arange(n_events, dtype=np.uint64) + np.uint64(rank * n_events))
+    ids = np.arange(n_events, dtype=np.uint64)
     return s, prim, ids, desc
 
 
@@ -196,7 +199,7 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    setup, prim, ids, desc = workload(args.workload, args.events, 0)
+    setup, prim, ids, desc = workload(args.workload, args.events)
     import oracle
     cores = len(os.sched_getaffinity(0))
     orc = oracle.Oracle(setup.materials, setup.physics, setup.layers, setup.world, setup.seed)
@@ -234,8 +237,12 @@ def gpu_arm(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     from paper_2203_09467_gb300 import emt
+    from paper_2203_09467_gb300 import shard
 
-    setup, prim, ids, desc = workload(args.workload, args.events, rank)
+    # one workload of world x events events, partitioned across the ranks
+    n_total = args.events * world
+    setup, prim_all, ids_all, desc = workload(args.workload, n_total)
+    mine, prim, ids = shard.local_shard(prim_all, ids_all, rank, world)
     n = len(ids)
     tune = None
     if args.loop == "auto":
@@ -335,6 +342,12 @@ def gpu_arm(args):
     h2d = sum(v.numel() * v.element_size() for v in pin.values()) + ids.nbytes
     d2h = hist_h.numel() * 8 + summ_h.numel() * 8
 
+    # the one gather of the sharded run: every event's results in event
+    # order (after the timed steps; no collective while stepping)
+    H, S = shard.gather_events(mine, hist_h.numpy(), summ_h.numpy(), n_total, world)
+    gather = {"events": int(len(S)), "events_with_deposit": int((S[:, 0] > 0).sum()),
+              "max_ledger_error": float(np.max(np.abs(S[:, 3] - S[:, 0] - S[:, 1] - S[:, 2]) / S[:, 3]))}
+
     # roofline of the step kernel
     peaks, src = load_peaks()
     kern_ms = sum(s["kernel_ms"] for s in stats)
@@ -373,36 +386,38 @@ def gpu_arm(args):
                 "algorithmic_fp64_inst_per_launch": inst * steps_per_launch,
                 "fp64_inst_per_track_step": inst, "kernel_share_of_step": kern_ms / total_ms}
 
-    # the plain form: the same events submitted and run one at a time
+    # the plain form: the same events submitted and run one at a time, with
+    # a host-driven step loop (one launch per step: the fused schedule suits
+    # a single event best) and with the persistent step loop
     forms = None
     if args.one_at_a_time > 0 and rank == 0:
         k = min(args.one_at_a_time, n)
-        # one launch per step (the fused schedule) suits a single event best
-        single = emt.context_for(setup, device=local, precision=args.precision, slot_capacity=1 << 22,
-                                 max_events=1, block_size=cfg["block_size"], loop_mode="plain",
-                                 schedule="fused")
         # primaries of event e: [first[e], first[e + 1]) (grouped by event)
         first = np.searchsorted(prim["event"], np.arange(n + 1))
-        steps1 = 0
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(single.stream)
-        for e in range(k):
-            lo, hi = int(first[e]), int(first[e + 1])
-            sub = {kk: v[lo:hi] for kk, v in dprim.items()}
-            sub["event"] = torch.zeros(hi - lo, dtype=torch.int32, device=dev)
-            single.submit(ids[e:e + 1], sub)
-            steps1 += single.run()["track_steps"]
-            single.read_all(hist_d[e:e + 1], summ_d[e:e + 1])
-        b.record(single.stream)
-        b.synchronize()
-        t1 = a.elapsed_time(b) / 1e3
-        single.close()
         forms = {"batched": {"events_per_s": n / (total_ms / 1e3 / args.steps), "track_steps_per_s": value / world,
-                             "config": cfg},
-                 "one_at_a_time": {"events_per_s": k / t1, "track_steps_per_s": steps1 / t1,
-                                   "sample_events": k}}
+                             "config": cfg}}
+        for name, loop in (("one_at_a_time", dict(loop_mode="plain")),
+                           ("one_at_a_time_persistent", dict(loop_mode="persistent", graph_steps=256))):
+            single = emt.context_for(setup, device=local, precision=args.precision, slot_capacity=1 << 22,
+                                     max_events=1, block_size=cfg["block_size"], schedule="fused", **loop)
+            steps1 = 0
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(single.stream)
+            for e in range(k):
+                lo, hi = int(first[e]), int(first[e + 1])
+                sub = {kk: v[lo:hi] for kk, v in dprim.items()}
+                sub["event"] = torch.zeros(hi - lo, dtype=torch.int32, device=dev)
+                single.submit(ids[e:e + 1], sub)
+                steps1 += single.run()["track_steps"]
+                single.read_all(hist_d[e:e + 1], summ_d[e:e + 1])
+            b.record(single.stream)
+            b.synchronize()
+            t1 = a.elapsed_time(b) / 1e3
+            single.close()
+            forms[name] = {"events_per_s": k / t1, "track_steps_per_s": steps1 / t1, "sample_events": k,
+                           "loop": loop["loop_mode"]}
 
     ctx.close()
     if args.diagnostics and rank == 0:
@@ -420,12 +435,14 @@ def gpu_arm(args):
         "config": {"workload": desc, "precision": args.precision, "schedule": cfg.get("schedule", "fused"),
                    "loop": cfg["loop_mode"],
                    "graph_steps": cfg["graph_steps"], "block": cfg["block_size"] or 256,
-                   "slot_capacity": args.slots, "events_per_gpu": n,
+                   "slot_capacity": args.slots, "events_per_gpu": n, "events_total": n_total,
+                   "partition": "one workload split across the GPUs by cost (greedy on primary energy)",
                    "l2": "512 MB buffer written between timed steps; track state >> L2"},
         "events_per_s": n * world / (total_ms_all / 1e3 / args.steps),
         "iterations_per_step": stats[0]["iterations"], "peak_tracks": max(s["peak_tracks"] for s in stats),
         "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": launches,
+        "gather": gather,
         "roofline": roof,
         "clocks": clk,
     }
@@ -477,23 +494,29 @@ def served_arm(args):
     setup.seed = 5
     rates = [float(r) for r in args.rates.split(",")]
     results = []
+    loops = args.serve_loops.split(",")
     for ri, rate in enumerate(rates):
         arrival = W.poisson_arrivals(rate, args.duration, seed=5 + ri)
         n = len(arrival)
         prim = W.served_primaries(n, seed=5 + ri)
         ids = np.arange(n, dtype=np.uint64) + np.uint64(1_000_000 * ri)
         row = {"rate_hz": rate, "requests": n, "duration_s": args.duration}
-        for mode in ("continuous", "batch"):
-            ctx = emt.context_for(setup, precision=args.precision, slot_capacity=args.serve_slots,
-                                  max_events=args.serve_events, loop_mode="graph", graph_steps=6)
-            admit, done, hist, summ = ctx.serve(ids, arrival, prim, mode=mode, steps_per_poll=6)
-            ctx.close()
-            lat = done - arrival
-            span = done.max() - arrival.min()
-            row[mode] = {"events_per_s": n / span, "p50_latency_s": float(np.percentile(lat, 50)),
-                         "p99_latency_s": float(np.percentile(lat, 99)),
-                         "mean_queue_s": float(np.mean(admit - arrival)),
-                         "track_steps": float(summ[:, 4].sum())}
+        for loop in loops:
+            for mode in ("continuous", "batch"):
+                # the graph driver replays 6 steps per launch; the persistent
+                # loop runs up to 6 steps per launch (or fewer, ending early)
+                ctx = emt.context_for(setup, precision=args.precision, slot_capacity=args.serve_slots,
+                                      max_events=args.serve_events, loop_mode=loop, graph_steps=6,
+                                      schedule="fused" if loop == "persistent" else "split")
+                admit, done, hist, summ = ctx.serve(ids, arrival, prim, mode=mode, steps_per_poll=6)
+                ctx.close()
+                lat = done - arrival
+                span = done.max() - arrival.min()
+                key = mode if loop == "graph" else f"{mode}_{loop}"
+                row[key] = {"events_per_s": n / span, "p50_latency_s": float(np.percentile(lat, 50)),
+                            "p99_latency_s": float(np.percentile(lat, 99)),
+                            "mean_queue_s": float(np.mean(admit - arrival)),
+                            "track_steps": float(summ[:, 4].sum()), "loop": loop}
         results.append(row)
         print(json.dumps(row), file=sys.stderr, flush=True)
     top = results[-1]
@@ -519,6 +542,8 @@ def main():
     ap.add_argument("--duration", type=float, default=60.0, help="served: seconds of requests per rate")
     ap.add_argument("--serve-slots", type=int, default=1 << 22, help="served: track-slot pool")
     ap.add_argument("--serve-events", type=int, default=4096, help="served: event slots")
+    ap.add_argument("--serve-loops", default="graph,persistent",
+                    help="served: step-loop drivers to compare (graph, persistent, plain)")
     ap.add_argument("--events", type=int, default=None, help="default 10,000 (100 for cms, cms_field)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--loop", default="auto", choices=["auto", "plain", "graph"],

@@ -88,6 +88,15 @@ typedef int32_t emt_status;
 /* step-loop driver of emt_run */
 #define EMT_LOOP_PLAIN 0 /* host loop: one kernel launch and one counter read per step */
 #define EMT_LOOP_GRAPH 1 /* CUDA graph of several steps; one counter read per graph */
+/* one persistent kernel (cooperative launch, fused step) runs up to
+ * graph_steps steps per launch with a grid barrier between steps and ends
+ * early when no track is left; one counter read per launch.  Removes the
+ * launch gaps between steps (the paper's many synchronization points per
+ * step, Sec. 3.2) where steps are short: one event at a time, the tail of
+ * a run, a served stream at a low rate.  Every barrier wait is bounded
+ * (10 s): a wait that gives up ends the launch and emt_run returns
+ * EMT_ERR_TIMEOUT (the context is then unusable). */
+#define EMT_LOOP_PERSISTENT 2
 
 /* how one step is laid out on the GPU (same results either way):
  * FUSED: one kernel; interacting tracks are regrouped by model inside each
@@ -107,7 +116,8 @@ typedef struct emt_options {
     int32_t max_bins;      /* histogram width capacity (>= emt_world.n_bins) */
     int32_t block_size;    /* threads per block of the step kernel: 128 or 256; 0 = 256 */
     int32_t loop_mode;     /* EMT_LOOP_* */
-    int32_t graph_steps;   /* steps per graph launch (EMT_LOOP_GRAPH); multiple of 6 */
+    int32_t graph_steps;   /* steps per graph launch (EMT_LOOP_GRAPH; multiple of 6) or per
+                              persistent launch (EMT_LOOP_PERSISTENT) */
     int32_t schedule;      /* EMT_SCHEDULE_*: how a step's interactions are grouped */
     uint32_t seed;         /* random stream seed */
     void* cuda_stream;     /* cudaStream_t to use, or NULL for a context-owned stream */
@@ -358,6 +368,16 @@ emt_status emt_serve(emt_ctx* ctx, int32_t n_events, const uint64_t* event_ids, 
  * second.  EMT_ERR_INVALID_ARG for non-positive counts, EMT_ERR_CUDA if
  * the device cannot run it. */
 emt_status emt_measure_dfma_rate(int32_t device, int32_t iters, int32_t repeats, double* fma_per_s);
+
+/* Diagnostics of the bounded device wait of EMT_LOOP_PERSISTENT (the
+ * paper has no counterpart): launches the same grid barrier on a device
+ * with one participant missing, so that its wait can only run out after
+ * timeout_ms (1..60000).  Returns EMT_ERR_TIMEOUT when the wait gave up,
+ * ended the kernel and reported it in the status word, as it must;
+ * EMT_OK would mean the barrier did not wait; EMT_ERR_INVALID_ARG for a
+ * bad timeout; EMT_ERR_CUDA on a CUDA failure.  Allocates and frees a few
+ * bytes of device memory of its own; the device stays usable. */
+emt_status emt_debug_wait_timeout(int32_t device, int32_t timeout_ms);
 
 /* Diagnostics: copy table (material m, particle p, quantity q) to host
  * out[n] (n = grid size).  gamma q: 0 photo, 1 compton, 2 pair;

@@ -5,9 +5,10 @@ interactions inside each block; split: a transport kernel and an
 interaction kernel joined by a queue in device memory), the block size (128
 or 256 threads: a larger block regroups more interacting tracks per model, a
 smaller one leaves more blocks per SM) and the step-loop driver (a host loop
-with one counter read per step, or CUDA graphs of 12 or 24 steps with one
-counter read per graph).  Every candidate transports the same batch of events; the
-fastest by CUDA-event time wins.  Results are cached per GPU name, workload
+with one counter read per step, CUDA graphs of 12 or 24 steps with one
+counter read per graph, or the persistent kernel that runs up to 64 or 256
+fused steps per launch with a grid barrier between steps).  Every candidate
+transports the same batch of events; the fastest by CUDA-event time wins.  Results are cached per GPU name, workload
 name and precision in a JSON file next to this module.
 """
 from __future__ import annotations
@@ -26,6 +27,10 @@ CANDIDATES = [
     for sched in ("fused", "split")
     for b in (128, 256)
     for loop, k in (("plain", 12), ("graph", 12), ("graph", 24))
+] + [
+    {"block_size": b, "loop_mode": "persistent", "graph_steps": k, "schedule": "fused"}
+    for b in (128, 256)
+    for k in (64, 256)
 ]
 
 

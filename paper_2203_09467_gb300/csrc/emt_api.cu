@@ -23,6 +23,10 @@ namespace {
 
 constexpr int kMaxGrid = 129;  // at most 128 intervals
 constexpr size_t kAlign = 256;
+// bound of one grid-barrier wait of the persistent step loop (a wait
+// outlasts the slowest block's step; steps of the populations the
+// persistent loop is meant for take milliseconds)
+constexpr double kPersistWaitMs = 10000.0;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
@@ -37,7 +41,7 @@ struct Plan {
     }
     // tracks: [side][field]
     size_t trk[2][11];
-    size_t cnt, status, total_steps, done_head, ehist;
+    size_t cnt, status, total_steps, done_head, ehist, gsync;
     size_t hist, ledger, counts, live, event_id, done_ring;
     size_t grid, gridf, igrid, igridf, irs, irsf, tab, tabf, dedx, mats, bk, vacuum, x0, ray_a, scratch;
     size_t dgrid, dgridf, dtab, dtabf;
@@ -75,6 +79,7 @@ Plan make_plan(const emt_options& o)
     p.total_steps = p.add(4 * sizeof(unsigned long long));
     p.done_head = p.add(sizeof(unsigned));
     p.ehist = p.add(3 * kEBins * sizeof(unsigned));
+    p.gsync = p.add(sizeof(GridSync));
     const size_t E = (size_t)p.max_events;
     p.hist = p.add(E * p.hstride * sizeof(double));
     p.ledger = p.add(E * 3 * sizeof(double));
@@ -145,7 +150,10 @@ bool valid_options(const emt_options& o, std::string& why)
     if (o.max_bins < 1 || o.max_bins > 65536) return why = "max_bins out of [1, 65536]", false;
     if (o.block_size != 0 && o.block_size != 128 && o.block_size != 256)
         return why = "block_size must be 0 (default), 128 or 256", false;
-    if (o.loop_mode != EMT_LOOP_PLAIN && o.loop_mode != EMT_LOOP_GRAPH) return why = "loop_mode", false;
+    if (o.loop_mode != EMT_LOOP_PLAIN && o.loop_mode != EMT_LOOP_GRAPH && o.loop_mode != EMT_LOOP_PERSISTENT)
+        return why = "loop_mode", false;
+    if (o.loop_mode == EMT_LOOP_PERSISTENT && o.graph_steps <= 0)
+        return why = "graph_steps (steps per persistent launch) must be positive", false;
     if (o.schedule != EMT_SCHEDULE_FUSED && o.schedule != EMT_SCHEDULE_SPLIT) return why = "schedule", false;
     if (o.loop_mode == EMT_LOOP_GRAPH && (o.graph_steps <= 0 || o.graph_steps % 6 != 0))
         return why = "graph_steps must be a positive multiple of 6", false;
@@ -242,6 +250,8 @@ struct emt_ctx {
     int64_t live_g = 0, live_c = 0;
     int resident_blocks = 0;
     int resident_a = 0, resident_b = 0;  // split schedule: transport, interaction kernels
+    int persist_grid = 0;                // persistent step loop: resident blocks of the cooperative launch
+    long long wait_cycles = 0;           // bound of one grid-barrier wait, SM clock cycles
     int block = 128;
     // host event table
     std::vector<uint64_t> slot_id;
@@ -629,6 +639,36 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
             if (r != EMT_OK) return r;
             ++done_it;
         }
+    } else if (c->opt.loop_mode == EMT_LOOP_PERSISTENT) {
+        // up to graph_steps steps per cooperative launch; the launch ends
+        // early when no track is left and reports how many steps it ran
+        GridSync* gs = c->at<GridSync>(pl.gsync);
+        while (c->live_g + c->live_c > 0 && budget_left()) {
+            const int k = max_iterations > 0 ? (int)std::min<int64_t>(c->opt.graph_steps, max_iterations - done_it)
+                                             : c->opt.graph_steps;
+            EMT_CUDA(c, cudaMemsetAsync(gs, 0, sizeof(GridSync), c->stream));
+            EMT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
+            cudaError_t e = Launch<R>::persist(p, c->it, k, gs, c->wait_cycles, c->persist_grid, c->block, c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "persistent step loop launch");
+            EMT_CUDA(c, cudaEventRecord(c->ev1, c->stream));
+            GridSync h_gs;
+            EMT_CUDA(c, cudaMemcpyAsync(&h_gs, gs, sizeof h_gs, cudaMemcpyDeviceToHost, c->stream));
+            EMT_CUDA(c, cudaMemcpyAsync(c->h_status, c->pool + pl.status, sizeof(int), cudaMemcpyDeviceToHost,
+                                        c->stream));
+            EMT_CUDA(c, cudaStreamSynchronize(c->stream));
+            if (*c->h_status & kStatusTimeout) {
+                // the steps of this launch are incomplete: the context's
+                // track state is no longer consistent
+                c->poisoned = true;
+                return fail(c, EMT_ERR_TIMEOUT, "persistent step loop: a grid barrier wait gave up");
+            }
+            s.kernel_launches += 1;
+            c->it += h_gs.iters;
+            s.iterations += h_gs.iters;
+            done_it += h_gs.iters;
+            emt_status r = read_counts();
+            if (r != EMT_OK) return r;
+        }
     } else {
         const int K = c->opt.graph_steps;
         while (c->live_g + c->live_c > 0 && budget_left()) {
@@ -830,6 +870,19 @@ emt_status emt_create(const emt_options* o, emt_ctx** out)
         };
         c->resident_a = std::max(1, dev_sms * blocks(0));
         c->resident_b = std::max(1, dev_sms * blocks(1));
+    }
+    if (o->loop_mode == EMT_LOOP_PERSISTENT) {
+        int coop = 0, clock_khz = 0;
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, o->device);
+        cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, o->device);
+        const int per = c->mixed() ? Launch<float>::persist_blocks_per_sm(c->block)
+                                   : Launch<double>::persist_blocks_per_sm(c->block);
+        if (!coop || per < 1 || clock_khz < 1) {
+            why = "the device cannot run the persistent step loop (cooperative launch)";
+            return bail(EMT_ERR_INVALID_ARG);
+        }
+        c->persist_grid = dev_sms * per;
+        c->wait_cycles = (long long)(kPersistWaitMs * (double)clock_khz);
     }
     c->slot_id.assign(pl.max_events, 0);
     c->slot_state.assign(pl.max_events, 0);
@@ -1315,6 +1368,30 @@ emt_status emt_debug_get_tracks(emt_ctx* c, int32_t cap, double* rec, uint64_t* 
     cudaFree(duid);
     cudaFree(dslot);
     return EMT_OK;
+}
+
+emt_status emt_debug_wait_timeout(int32_t device, int32_t timeout_ms)
+{
+    if (timeout_ms < 1 || timeout_ms > 60000) return EMT_ERR_INVALID_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return EMT_ERR_CUDA;
+    int clock_khz = 0;
+    if (cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, device) != cudaSuccess || clock_khz < 1)
+        return EMT_ERR_CUDA;
+    char* buf = nullptr;
+    cudaStream_t st = nullptr;
+    emt_status rc = EMT_ERR_CUDA;
+    int status = 0;
+    const size_t bytes = 256 + sizeof(int);
+    if (cudaMalloc(&buf, bytes) == cudaSuccess && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
+        cudaMemsetAsync(buf, 0, bytes, st) == cudaSuccess &&
+        launch_wait_never(reinterpret_cast<GridSync*>(buf), (long long)timeout_ms * clock_khz,
+                          reinterpret_cast<int*>(buf + 256), 2, st) == cudaSuccess &&
+        cudaMemcpyAsync(&status, buf + 256, sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+        cudaStreamSynchronize(st) == cudaSuccess)
+        rc = (status & kStatusTimeout) ? EMT_ERR_TIMEOUT : EMT_OK;
+    if (st) cudaStreamDestroy(st);
+    if (buf) cudaFree(buf);
+    return rc;
 }
 
 }  // extern "C"

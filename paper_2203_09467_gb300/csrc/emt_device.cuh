@@ -48,6 +48,7 @@ constexpr double kHbarC = 197.3269804e-13;   // hbar c, MeV cm (CODATA 2018)
 constexpr uint32_t kMscDraw = 1u << 20;  // draw index of the two msc uniforms of a step
 constexpr int kStatusQueueOverflow = 1;
 constexpr int kStatusBadTrack = 2;
+constexpr int kStatusTimeout = 4;  // a bounded device wait gave up (persistent step loop)
 
 // ------------------------------------------------------------------ math
 __device__ __forceinline__ double mlog(double x) { return log(x); }
@@ -123,6 +124,15 @@ struct Tracks {
 // c holds the tracks whose estimated RK4 substep count n satisfies
 // (kMaxSubsteps - n) >> 2 == c, so class 0 is the most expensive
 constexpr int kSortKeys = 32;
+
+// state of the grid barrier of the persistent step loop (zeroed before
+// each launch)
+struct GridSync {
+    unsigned count;  // blocks arrived at the current barrier
+    unsigned gen;    // barriers completed
+    unsigned iters;  // steps run by the launch
+    unsigned pad;
+};
 
 // per-iteration counters, rotating over three slots (input, output, clear)
 struct Counters {

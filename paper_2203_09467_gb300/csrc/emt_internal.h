@@ -58,6 +58,15 @@ struct Launch {
     static int max_blocks_split(int block, int which);
     // host spill: append n tracks of the spill buffer to side `side`
     static cudaError_t unspill(const Params<R>& p, int side, int cs, int n, cudaStream_t st);
+    // persistent step loop (fused schedule, cooperative launch of `grid`
+    // resident blocks): up to max_steps steps from global iteration it0
+    static cudaError_t persist(const Params<R>& p, long long it0, int max_steps, GridSync* gs,
+                               long long limit_cycles, int grid, int block, cudaStream_t st);
+    static int persist_blocks_per_sm(int block);
 };
+
+// diagnostics: a bounded grid wait that is never released (on `blocks`
+// blocks); sets kStatusTimeout in *status once it gives up
+cudaError_t launch_wait_never(GridSync* gs, long long limit_cycles, int* status, int blocks, cudaStream_t st);
 
 }  // namespace emt

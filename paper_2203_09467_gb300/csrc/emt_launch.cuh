@@ -45,6 +45,63 @@ cudaError_t Launch<R>::step(const Params<R>& p, int side, int cin, int cout, int
     return cudaGetLastError();
 }
 
+template <typename R, int BS, int G, bool X>
+static cudaError_t launch_persist_x(const Params<R>& p, long long it0, int max_steps, GridSync* gs,
+                                   long long limit_cycles, int grid, cudaStream_t st)
+{
+    Params<R> pc = p;
+    void* args[] = {&pc, &it0, &max_steps, &gs, &limit_cycles};
+    return cudaLaunchCooperativeKernel((const void*)k_persist<R, BS, G, X>, dim3(grid), dim3(BS), args, 0, st);
+}
+
+template <typename R>
+cudaError_t Launch<R>::persist(const Params<R>& p, long long it0, int max_steps, GridSync* gs,
+                               long long limit_cycles, int grid, int block, cudaStream_t st)
+{
+    const bool cyl = p.geom == kGeomCylinders;
+    const bool x = extended(p);
+    if (block == 128) {
+        if (cyl)
+            return x ? launch_persist_x<R, 128, kGeomCylinders, true>(p, it0, max_steps, gs, limit_cycles, grid, st)
+                     : launch_persist_x<R, 128, kGeomCylinders, false>(p, it0, max_steps, gs, limit_cycles, grid, st);
+        return x ? launch_persist_x<R, 128, kGeomLayers, true>(p, it0, max_steps, gs, limit_cycles, grid, st)
+                 : launch_persist_x<R, 128, kGeomLayers, false>(p, it0, max_steps, gs, limit_cycles, grid, st);
+    }
+    if (block == 256) {
+        if (cyl)
+            return x ? launch_persist_x<R, 256, kGeomCylinders, true>(p, it0, max_steps, gs, limit_cycles, grid, st)
+                     : launch_persist_x<R, 256, kGeomCylinders, false>(p, it0, max_steps, gs, limit_cycles, grid, st);
+        return x ? launch_persist_x<R, 256, kGeomLayers, true>(p, it0, max_steps, gs, limit_cycles, grid, st)
+                 : launch_persist_x<R, 256, kGeomLayers, false>(p, it0, max_steps, gs, limit_cycles, grid, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// resident blocks per SM of the persistent kernel, the smallest over its
+// instantiations (every block of a cooperative launch must be resident)
+template <typename R, int BS>
+static int min_blocks_persist()
+{
+    int n[4] = {0, 0, 0, 0};
+    cudaError_t e[4];
+    e[0] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[0], k_persist<R, BS, kGeomLayers, false>, BS, 0);
+    e[1] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[1], k_persist<R, BS, kGeomCylinders, false>, BS, 0);
+    e[2] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[2], k_persist<R, BS, kGeomLayers, true>, BS, 0);
+    e[3] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[3], k_persist<R, BS, kGeomCylinders, true>, BS, 0);
+    int m = 1 << 30;
+    for (int k = 0; k < 4; ++k) {
+        if (e[k] != cudaSuccess) return 0;
+        if (n[k] < m) m = n[k];
+    }
+    return m;
+}
+
+template <typename R>
+int Launch<R>::persist_blocks_per_sm(int block)
+{
+    return block == 128 ? min_blocks_persist<R, 128>() : min_blocks_persist<R, 256>();
+}
+
 template <typename R>
 cudaError_t Launch<R>::admit(const Params<R>& p, int side, int cs, int n, const int32_t* ev, const int32_t* type,
                              const double* T, const double* pos, const double* dir, const uint32_t* slot_of_event,

@@ -693,10 +693,9 @@ struct Staging {
 // Only interactions make two outputs.  When 2n <= Q every step fits and no
 // token is counted.
 template <typename R, int BS, int G, bool X>
-__global__ void __launch_bounds__(BS, 512 / BS) k_step(Params<R> p, int side, int cin, int cout, int cclr)
+__device__ __forceinline__ void step_body(const Params<R>& p, int side, int cin, int cout, int cclr, int& s_chunk,
+                                          Staging<R, BS>& sg)
 {
-    __shared__ int s_chunk;
-    __shared__ Staging<R, BS> sg;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         p.cnt[cclr] = Counters{};
     }
@@ -846,6 +845,84 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_step(Params<R> p, int side, in
         __syncthreads();
     }
 }
+
+template <typename R, int BS, int G, bool X>
+__global__ void __launch_bounds__(BS, 512 / BS) k_step(Params<R> p, int side, int cin, int cout, int cclr)
+{
+    __shared__ int s_chunk;
+    __shared__ Staging<R, BS> sg;
+    step_body<R, BS, G, X>(p, side, cin, cout, cclr, s_chunk, sg);
+}
+
+// Grid-wide barrier of a persistent kernel whose blocks are all resident
+// (cooperative launch): every block's thread 0 arrives on a counter, the
+// last one resets it and advances the generation, the others wait for the
+// generation to change.  The wait is bounded: after limit_cycles SM clock
+// cycles (or once another block has given up) the block sets
+// kStatusTimeout in the status word and returns false, so that the kernel
+// ends and the host reports EMT_ERR_TIMEOUT instead of spinning forever.
+__device__ __forceinline__ bool grid_barrier(GridSync* gs, unsigned blocks, long long limit_cycles, int* status)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned* gen = &gs->gen;
+        volatile int* vstatus = status;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(&gs->count, 1u) + 1u == blocks) {
+            gs->count = 0u;
+            __threadfence();
+            atomicAdd(&gs->gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == g) {
+                if ((*vstatus & kStatusTimeout) || clock64() - t0 > limit_cycles) {
+                    atomicOr(status, kStatusTimeout);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Persistent step loop: up to max_steps steps of the fused schedule in one
+// launch, from global iteration it0 (its counter slots and ping-pong side),
+// with a grid barrier after each step; the launch ends early when no track
+// is left.  Removes the launch gap between steps (the paper's many
+// synchronization points per step, Sec. 3.2) where a step is short: the
+// tail of a run, one event at a time, a served stream at a low rate.
+// gs->iters receives the number of steps run.
+template <typename R, int BS, int G, bool X>
+__global__ void __launch_bounds__(BS, 512 / BS)
+    k_persist(Params<R> p, long long it0, int max_steps, GridSync* gs, long long limit_cycles)
+{
+    __shared__ int s_chunk;
+    __shared__ Staging<R, BS> sg;
+    __shared__ int s_go;
+    int done = 0;
+    while (done < max_steps) {
+        const long long it = it0 + done;
+        const int side = (int)(it & 1), cin = (int)(it % 3), cout = (int)((it + 1) % 3), cclr = (int)((it + 2) % 3);
+        step_body<R, BS, G, X>(p, side, cin, cout, cclr, s_chunk, sg);
+        ++done;
+        if (!grid_barrier(gs, gridDim.x, limit_cycles, p.status)) return;
+        if (threadIdx.x == 0) s_go = p.cnt[cout].n[0] + p.cnt[cout].n[1] > 0;
+        __syncthreads();
+        const bool go = s_go != 0;
+        __syncthreads();
+        if (!go) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) gs->iters = (unsigned)done;
+}
+
 
 // Admit primaries (structure of arrays, device memory) into side `side`,
 // appending after the tracks already counted in slot `cs`.  Primaries

@@ -16,7 +16,7 @@ from . import build as _build
 
 HOST, DEVICE = 0, 1
 PRECISION = {"fp64": 0, "mixed": 1}
-LOOP = {"plain": 0, "graph": 1}
+LOOP = {"plain": 0, "graph": 1, "persistent": 2}
 SCHEDULE = {"fused": 0, "split": 1}
 SELECT = {"order": 0, "low_energy": 1}
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "CAPACITY", -3: "CUDA", -4: "BAD_STATE", -5: "TIMEOUT",
@@ -124,6 +124,7 @@ _SIGS = {
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(Primaries),
                                    ctypes.POINTER(ServeOptions), ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p]),
+    "emt_debug_wait_timeout": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32]),
     "emt_measure_dfma_rate": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                ctypes.POINTER(ctypes.c_double)]),
     "emt_transport_static": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_uint32, ctypes.POINTER(Material),

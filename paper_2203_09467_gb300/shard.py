@@ -45,23 +45,35 @@ def shard_primaries(prim, events):
     return {k: v[order] for k, v in out.items()}
 
 
-def run_sharded(engine, prim, event_ids, rank, world, group=None):
-    """Transport this rank's shard with engine(prim, ids) -> (hist, summary)
-    and gather every rank's results on every rank, in the original event
-    order.  With world == 1 no collective is used."""
+def local_shard(prim, event_ids, rank, world):
+    """This rank's events of one workload (cost-balanced partition): the
+    original event indices, their primaries (renumbered) and their ids."""
     n = len(event_ids)
-    parts = partition_by_cost(event_costs(prim, n), world)
-    mine = parts[rank]
-    hist, summ = engine(shard_primaries(prim, mine), np.asarray(event_ids)[mine])
+    mine = partition_by_cost(event_costs(prim, n), world)[rank]
+    return mine, shard_primaries(prim, mine), np.asarray(event_ids)[mine]
+
+
+def gather_events(mine, hist, summ, n_events, world, group=None):
+    """The one gather of a sharded run: every rank's per-event results,
+    placed in the original event order on every rank.  With world == 1 no
+    collective is used."""
     if world == 1:
         return hist, summ
     import torch.distributed as dist
     gathered = [None] * world
-    dist.all_gather_object(gathered, (mine, hist, summ), group=group)
-    nb = hist.shape[1]
-    H = np.zeros((n, nb))
-    S = np.zeros((n, summ.shape[1]))
+    dist.all_gather_object(gathered, (np.asarray(mine), np.asarray(hist), np.asarray(summ)), group=group)
+    H = np.zeros((n_events, np.asarray(hist).shape[1]))
+    S = np.zeros((n_events, np.asarray(summ).shape[1]))
     for idx, h, s in gathered:
         H[idx] = h
         S[idx] = s
     return H, S
+
+
+def run_sharded(engine, prim, event_ids, rank, world, group=None):
+    """Transport this rank's shard with engine(prim, ids) -> (hist, summary)
+    and gather every rank's results on every rank, in the original event
+    order.  With world == 1 no collective is used."""
+    mine, p, ids = local_shard(prim, event_ids, rank, world)
+    hist, summ = engine(p, ids)
+    return gather_events(mine, hist, summ, len(event_ids), world, group)

@@ -18,6 +18,16 @@ def emt():
     return E
 
 
+def overlapping_admissions(admit, done):
+    """Requests admitted while an earlier-admitted request was still on the
+    GPU (admitted, not yet finished)."""
+    n = 0
+    for j in range(len(admit)):
+        earlier = admit < admit[j]
+        n += int(np.any(earlier & (done > admit[j])))
+    return n
+
+
 def alone(emt, s, prim, e, event_id, **kw):
     sub = W.subset(prim, [e])
     ctx = emt.context_for(s, slot_capacity=1 << 20, max_events=1, **kw)
@@ -41,6 +51,8 @@ def test_served_results_equal_alone(emt, precision):
     assert ctx.events_in_flight() == 0
     ctx.close()
     assert np.all(admit >= arrival - 1e-3) and np.all(done >= admit)
+    # continuous batching: requests were admitted while others were in flight
+    assert overlapping_admissions(admit, done) > 0
     # the ledger closes on every event (FP64 exactly; mixed to FP32 rounding)
     led = np.abs(summ[:, 3] - summ[:, 0] - summ[:, 1] - summ[:, 2]) / summ[:, 3]
     assert led.max() < (1e-9 if precision == "fp64" else 1e-5)
@@ -62,5 +74,9 @@ def test_batch_schedule_matches_continuous(emt):
         ctx = emt.context_for(s, slot_capacity=1 << 21, max_events=8)
         out[mode] = ctx.serve(ids, arrival, prim, mode=mode, steps_per_poll=4)
         ctx.close()
+    # one batch at a time: nothing is admitted while an earlier batch runs;
+    # continuously: requests join the events in flight
+    assert overlapping_admissions(out["batch"][0], out["batch"][1]) == 0
+    assert overlapping_admissions(out["continuous"][0], out["continuous"][1]) > 0
     assert np.array_equal(out["continuous"][3][:, 4:], out["batch"][3][:, 4:])
     assert np.allclose(out["continuous"][3][:, :4], out["batch"][3][:, :4], rtol=1e-12, atol=0)

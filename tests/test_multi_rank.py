@@ -79,3 +79,24 @@ def test_rank_without_events(tmp_path):
     for r in range(world):
         assert np.array_equal(np.load(tmp_path / f"h{r}.npy"), H1)
         assert np.array_equal(np.load(tmp_path / f"s{r}.npy"), S1)
+
+
+def test_local_shards_cover_one_workload_once():
+    """The benchmark's split of one workload: the ranks' shards are disjoint,
+    cover every event, keep each event's primaries together and in order,
+    and carry near-equal primary energy."""
+    s, prim, ids = _setup(n=400)
+    world = 4
+    seen = []
+    loads = []
+    for r in range(world):
+        mine, p, local_ids = shard.local_shard(prim, ids, r, world)
+        seen.extend(mine.tolist())
+        assert np.array_equal(local_ids, ids[mine])
+        assert np.array_equal(np.unique(p["event"]), np.arange(len(mine)))
+        for k, e in enumerate(mine[:20]):
+            want = prim["T"][prim["event"] == e]
+            assert np.array_equal(p["T"][p["event"] == k], want)
+        loads.append(p["T"].sum())
+    assert sorted(seen) == list(range(400))
+    assert max(loads) / min(loads) < 1.02
