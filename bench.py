@@ -42,22 +42,25 @@ from paper_2203_09467_gb300 import workloads as W  # noqa: E402
 
 METRIC = "track-steps/s"
 
-# Per track-step figures of the step kernels from one ncu capture of every
-# k_transport and k_interact launch of a smaller run of the same workload
-# (the summary and the command are in profiles/): DRAM traffic
-# (dram__bytes_read.sum + dram__bytes_write.sum) and FP64-pipe work
-# (sm__thread_inst_executed_pipe_fp64_pred_on.sum, the kernels' FP64
-# arithmetic as compiled: nothing is recomputed).  They are reported only
-# while the kernel sources are the ones that were measured (SHA-256 below).
+# DRAM traffic per track-step of the step kernels (dram__bytes_read.sum +
+# dram__bytes_write.sum from ncu captures of a few launches of each step
+# kernel on a smaller run of the same workload, scaled by the launches'
+# track counts; summary and commands in profiles/).  Reported only while
+# the kernel sources are the ones that were measured (SHA-256 below).
 TRAFFIC = {
-    "kernel_sha256": "c46928af7038add72deb3317136261db115ed2e5864818097fee0ac0a36750b3",
-    "bytes_per_track_step": {"calo/fp64": 128.20, "calo/mixed": 85.18},
-    "fp64_inst_per_track_step": {"calo/fp64": 86.87, "calo/mixed": 25.82},
+    "kernel_sha256": "",
+    "bytes_per_track_step": {},
     "source": "profiles/step_kernels_calo_dram_traffic.md",
 }
-# FP64 pipe peak: 1.25 TFLOP/s nominal FP64 on GB300 (an FMA counts two
-# flops) = 625 G FP64 thread-instructions/s (152 SMs x 2 per clock x ~2.06 GHz)
-FP64_PEAK_GINST = 625.0
+# Algorithmic FP64 work of one track-step of the method, fixed by its
+# definition: a census of the FP64 operations of the oracle's step on the
+# workload (oracle/census.py; summary in profiles/fp64_census_of_the_step.md),
+# in flops with add, sub, mul, div and sqrt one each and an fma two
+# (comparisons and elementary functions are listed there, not counted).  It
+# does not change when the kernels are optimised.
+FLOPS_PER_TRACK_STEP = {"calo": 43.09, "calo_field": 967.93, "cms": 73.49}
+# nominal FP64 peak of GB300: 152 SMs x 2 DFMA per clock x 2 flops x 2.06 GHz
+FP64_NOMINAL_GFLOPS = 1252.5
 KERNEL_SOURCES = ["emt_device.cuh", "emt_step.cuh", "emt_split.cuh", "emt_launch.cuh", "emt_kernels_fp64.cu",
                   "emt_kernels_mixed.cu"]
 
@@ -189,10 +192,22 @@ def cpu_baseline(setup, prim, ids, budget_s=12.0):
         if t > budget_s:
             break
         n = min(n_total - done, int(take * max(1.0, min(4.0, budget_s / max(t, 1e-3) / 2)))) or 1
+    # one core: the first events of the workload for about a quarter of the budget
+    t1, steps1, done1 = 0.0, 0.0, 0
+    while done1 < n_total and t1 < budget_s / 4:
+        take = min(max(1, cores), n_total - done1)
+        sub = W.subset(prim, np.arange(done1, done1 + take))
+        t0 = time.perf_counter()
+        _, summ = orc.run(sub, take, ids[done1:done1 + take], n_threads=1)
+        t1 += time.perf_counter() - t0
+        steps1 += summ[:, 4].sum()
+        done1 += take
     orc.close()
     return {"value": steps / t, "unit": METRIC, "cores": cores, "kind": "oracle",
             "sample": f"first {done} of {n_total} events of the workload, {int(steps)} track-steps, "
-                      f"{t:.1f} s on {cores} threads"}
+                      f"{t:.1f} s on {cores} threads",
+            "value_1core": steps1 / t1,
+            "sample_1core": f"first {done1} events, {int(steps1)} track-steps, {t1:.1f} s on 1 thread"}
 
 
 def reference_arm(args):
@@ -349,6 +364,7 @@ def gpu_arm(args):
               "max_ledger_error": float(np.max(np.abs(S[:, 3] - S[:, 0] - S[:, 1] - S[:, 2]) / S[:, 3]))}
 
     # roofline of the step kernel
+    dfma = emt.measure_dfma_rate(local)  # FP64 FMAs per second, measured now on this GPU
     peaks, src = load_peaks()
     kern_ms = sum(s["kernel_ms"] for s in stats)
     kern_launch = sum(s["iterations"] for s in stats)  # one step-loop iteration = one step (1 or 2 kernels)
@@ -371,20 +387,26 @@ def gpu_arm(args):
         roof["traffic"] = per_step * steps_per_launch
         roof["traffic_source"] = (f"{TRAFFIC['source']}: {per_step:.1f} B per track-step x "
                                   f"{steps_per_launch:.0f} track-steps per launch")
-    inst = TRAFFIC["fp64_inst_per_track_step"].get(key) if current else None
+    flops = FLOPS_PER_TRACK_STEP.get(args.workload)
     roof_hbm = None
-    if inst:
-        # the step kernels are bound by the FP64 pipe: report that roofline,
-        # and the HBM one beside it
+    if flops and args.precision == "fp64":
+        # the FP64 step kernels are led by the FP64 pipe: report the
+        # arithmetic roofline (algorithmic flops per track-step from the
+        # census of the method), and the HBM one beside it
         roof_hbm = roof
-        ach = inst * steps_done / (kern_ms / 1e3) / 1e9
-        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GINST, "unit": "G FP64 inst/s",
-                "frac": ach / FP64_PEAK_GINST, "traffic": roof_hbm["traffic"],
-                "peak_source": "nominal 1.25 TFLOP/s FP64 of GB300 = 625 G FP64 thread-instructions/s",
+        ach = flops * steps_done / (kern_ms / 1e3) / 1e9
+        peak_f = 2.0 * dfma / 1e9
+        roof = {"bound": "alu", "achieved": ach, "peak": peak_f, "unit": "GFLOP/s",
+                "frac": ach / peak_f, "traffic": roof_hbm["traffic"],
+                "peak_source": f"measured now: {dfma / 1e9:.1f} G DFMA/s (emt_measure_dfma_rate, independent "
+                               "chains) x 2 flops",
+                "frac_of_nominal": ach / FP64_NOMINAL_GFLOPS, "peak_nominal": FP64_NOMINAL_GFLOPS,
                 "kernel": roof_hbm["kernel"], "launches": kern_launch,
                 "mean_launch_ms": kern_ms / max(kern_launch, 1),
-                "algorithmic_fp64_inst_per_launch": inst * steps_per_launch,
-                "fp64_inst_per_track_step": inst, "kernel_share_of_step": kern_ms / total_ms}
+                "algorithmic_flops_per_launch": flops * steps_per_launch,
+                "flops_per_track_step": flops,
+                "flops_source": "census of the oracle's step (oracle/census.py)",
+                "kernel_share_of_step": kern_ms / total_ms}
 
     # the plain form: the same events submitted and run one at a time, with
     # a host-driven step loop (one launch per step: the fused schedule suits

@@ -1,8 +1,9 @@
 """FP64 CPU oracle of the EM transport loop (arXiv:2203.09467, Secs. 2.1-3.2).
 
-TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
-CPU-baseline leg of the benchmark import this package.  It shares no code
-with the GPU library and imports nothing from it.
+TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check, the
+CPU-baseline leg of the benchmark and oracle/census.py (a count of the
+step's FP64 operations) import this package.  It shares no code with the
+GPU library and imports nothing from it.
 
 Functions without a pin: absolute agreement of the closed-form physics with
 measured data or Geant4 is "parity unpinned" (no data to check it is
@@ -54,56 +55,59 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def bind(L):
+    """Declare the oracle's C functions on a loaded library (ctypes)."""
+    d, u32, u64, i32, p = (ctypes.c_double, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p)
+    sig = {
+        "orc_philox4x32_10": (None, [p, p, p]),
+        "orc_track_uniform": (d, [u32, u64, u64, u32, u32]),
+        "orc_child_uid": (u64, [u32, u64, u64, u32, u32]),
+        "orc_x0_gcm2": (d, [d, d]),
+        "orc_sigma_kn": (d, [d]),
+        "orc_dsigma_kn_deps": (d, [d, d]),
+        "orc_sigma_pair_atom": (d, [d, d, d]),
+        "orc_dsigma_pair_dx": (d, [d, d, d, d]),
+        "orc_sigma_photo_atom": (d, [d, d, d]),
+        "orc_sigma_moller": (d, [d, d]),
+        "orc_dsigma_moller_deps": (d, [d, d]),
+        "orc_sigma_bhabha": (d, [d, d]),
+        "orc_dsigma_bhabha_deps": (d, [d, d]),
+        "orc_sigma_heitler": (d, [d]),
+        "orc_dsigma_heitler_deps": (d, [d, d]),
+        "orc_sigma_brems_macro": (d, [d, d, d]),
+        "orc_dsigma_brems_macro_dk": (d, [d, d, d]),
+        "orc_dedx_rad": (d, [d, d, d]),
+        "orc_dedx_coll": (d, [d, d, d, d, i32, d, d]),
+        "orc_gauss_legendre": (None, [i32, p, p]),
+        "orc_sample": (i32, [i32, d, d, d, u32, u64, u64, u32, p]),
+        "orc_highland": (d, [d, d, d]),
+        "orc_sigma_rayleigh_atom": (d, [d, d]),
+        "orc_dsigma_rayleigh_dx": (d, [d, d, d]),
+        "orc_msc": (i32, [d, d, d, u32, u64, u64, u32, p]),
+        "orc_create": (p, [p, i32, p, p, i32, p, u32]),
+        "orc_destroy": (None, [p]),
+        "orc_grid_size": (i32, [p]),
+        "orc_get_table": (i32, [p, i32, i32, i32, p]),
+        "orc_range": (d, [p, i32, i32, d]),
+        "orc_inv_range": (d, [p, i32, i32, d]),
+        "orc_run": (i32, [p, i32, p, p, p, p, p, i32, p, p, p, i32, p, i32]),
+        "orc_nav_exit": (i32, [p, i32, p, p, p]),
+        "orc_locate": (i32, [p, p]),
+        "orc_step_one": (i32, [p, p, u64, u64, p, p, p]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            L = ctypes.CDLL(_LIB)
-            d, u32, u64, i32, p = (ctypes.c_double, ctypes.c_uint32, ctypes.c_uint64,
-                                   ctypes.c_int, ctypes.c_void_p)
-            sig = {
-                "orc_philox4x32_10": (None, [p, p, p]),
-                "orc_track_uniform": (d, [u32, u64, u64, u32, u32]),
-                "orc_child_uid": (u64, [u32, u64, u64, u32, u32]),
-                "orc_x0_gcm2": (d, [d, d]),
-                "orc_sigma_kn": (d, [d]),
-                "orc_dsigma_kn_deps": (d, [d, d]),
-                "orc_sigma_pair_atom": (d, [d, d, d]),
-                "orc_dsigma_pair_dx": (d, [d, d, d, d]),
-                "orc_sigma_photo_atom": (d, [d, d, d]),
-                "orc_sigma_moller": (d, [d, d]),
-                "orc_dsigma_moller_deps": (d, [d, d]),
-                "orc_sigma_bhabha": (d, [d, d]),
-                "orc_dsigma_bhabha_deps": (d, [d, d]),
-                "orc_sigma_heitler": (d, [d]),
-                "orc_dsigma_heitler_deps": (d, [d, d]),
-                "orc_sigma_brems_macro": (d, [d, d, d]),
-                "orc_dsigma_brems_macro_dk": (d, [d, d, d]),
-                "orc_dedx_rad": (d, [d, d, d]),
-                "orc_dedx_coll": (d, [d, d, d, d, i32, d, d]),
-                "orc_gauss_legendre": (None, [i32, p, p]),
-                "orc_sample": (i32, [i32, d, d, d, u32, u64, u64, u32, p]),
-                "orc_highland": (d, [d, d, d]),
-                "orc_sigma_rayleigh_atom": (d, [d, d]),
-                "orc_dsigma_rayleigh_dx": (d, [d, d, d]),
-                "orc_msc": (i32, [d, d, d, u32, u64, u64, u32, p]),
-                "orc_create": (p, [p, i32, p, p, i32, p, u32]),
-                "orc_destroy": (None, [p]),
-                "orc_grid_size": (i32, [p]),
-                "orc_get_table": (i32, [p, i32, i32, i32, p]),
-                "orc_range": (d, [p, i32, i32, d]),
-                "orc_inv_range": (d, [p, i32, i32, d]),
-                "orc_run": (i32, [p, i32, p, p, p, p, p, i32, p, p, p, i32, p, i32]),
-                "orc_nav_exit": (i32, [p, i32, p, p, p]),
-                "orc_locate": (i32, [p, p]),
-                "orc_step_one": (i32, [p, p, u64, u64, p, p, p]),
-            }
-            for name, (res, args) in sig.items():
-                f = getattr(L, name)
-                f.restype = res
-                f.argtypes = args
-            _lib = L
+            _lib = bind(ctypes.CDLL(_LIB))
     return _lib
 
 

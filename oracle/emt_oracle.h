@@ -4,8 +4,9 @@
  *
  * TEST INFRASTRUCTURE ONLY.  This code exists to check the GPU library; it is
  * called from the test suite, from the smoke check and from the CPU-baseline
- * leg of the benchmark, and from nothing else.  It shares no code with the
- * CUDA path.
+ * leg of the benchmark, and compiled by oracle/census.cpp (a count of the
+ * step's FP64 operations), and from nothing else.  It shares no code with
+ * the CUDA path.
  *
  * The paper names the physics models (Sec. 2.2, Table 1) and capabilities
  * (material properties, continuous slowing down, competing discrete
