@@ -316,13 +316,20 @@ __global__ void __launch_bounds__(BS, transport_threads_per_sm<R>() / BS)
     }
 }
 
+// Queue records per thread in one chunk of the interaction kernel: a block
+// counting-sorts kInteractRecords * BS records by model and its warps take
+// them in sorted order, kInteractRecords rounds of 32 each; larger sorted
+// chunks give warps of fewer models.
+constexpr int kInteractRecords = 2;
+
 template <typename R, int BS, bool S, bool X>
 __global__ void __launch_bounds__(BS, 512 / BS) k_interact(Params<R> p, int side, int cin, int cout)
 {
+    constexpr int CH = BS * kInteractRecords;
     __shared__ int s_chunk;
     __shared__ int count[kNumModels];
     __shared__ int offset[kNumModels + 1];
-    __shared__ unsigned short perm[BS];
+    __shared__ unsigned short perm[CH];
     __shared__ unsigned s_eh[S ? kEBins : 1];
     constexpr bool select = S;
     if constexpr (select) {
@@ -336,7 +343,7 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_interact(Params<R> p, int side
     const long long spare = Q - ntot;
     const bool unlimited = 2 * ntot <= Q;
     const int n_int = p.cnt[cin].n_int;
-    const int chunks = (n_int + BS - 1) / BS;
+    const int chunks = (n_int + CH - 1) / CH;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const unsigned lanes_below = (1u << lane) - 1u;
@@ -349,13 +356,19 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_interact(Params<R> p, int side
         __syncthreads();
         const int chunk = s_chunk;
         if (chunk >= chunks) break;
-        const long long r0 = (long long)chunk * BS;
-        const int n_here = (int)(n_int - r0 < BS ? n_int - r0 : BS);
+        const long long r0 = (long long)chunk * CH;
+        const int n_here = (int)(n_int - r0 < CH ? n_int - r0 : CH);
         // counting sort of the chunk's records by model
-        int model = -1, rank = 0;
-        if (tid < n_here) {
-            model = (int)(iq.tv[r0 + tid] >> 24);
-            rank = atomicAdd(&count[model], 1);
+        int model[kInteractRecords], rank[kInteractRecords];
+#pragma unroll
+        for (int j = 0; j < kInteractRecords; ++j) {
+            const int idx = j * BS + tid;
+            model[j] = -1;
+            rank[j] = 0;
+            if (idx < n_here) {
+                model[j] = (int)(iq.tv[r0 + idx] >> 24);
+                rank[j] = atomicAdd(&count[model[j]], 1);
+            }
         }
         __syncthreads();
         if (tid == 0) {
@@ -367,72 +380,77 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_interact(Params<R> p, int side
             offset[kNumModels] = acc;
         }
         __syncthreads();
-        if (model >= 0) perm[offset[model] + rank] = (unsigned short)tid;
+#pragma unroll
+        for (int j = 0; j < kInteractRecords; ++j)
+            if (model[j] >= 0) perm[offset[model[j]] + rank[j]] = (unsigned short)(j * BS + tid);
         __syncthreads();
 
-        const bool mine = tid < n_here;
-        TrackReg<R> t;
-        Effects fx;
-        StepOut<R> o;
-        o.n = 0;
-        bool stepped = false;
-        long long rsrc = 0;
-        if (mine) {
-            const long long r = r0 + perm[tid];
-            const uint32_t tv = iq.tv[r];
-            t.x[0] = iq.x[r];
-            t.x[1] = iq.y[r];
-            t.x[2] = iq.z[r];
-            t.u[0] = iq.ux[r];
-            t.u[1] = iq.uy[r];
-            t.u[2] = iq.uz[r];
-            t.T = iq.T[r];
-            t.uid = iq.uid[r];
-            t.ev = iq.ev[r];
-            t.step = iq.step[r];
-            t.type = (int)(tv & 0xFFu);
-            t.vol = (int)((tv >> 8) & 0xFFFFu) - 2;
-            rsrc = iq.src[r];
-            fx.dep = iq.dep[r];
-            fx.esc = 0.0;
-            fx.kill = 0.0;
-            fx.col = score_col(p, t.vol, t.x[2]);
-            fx.finished = false;
-            fx.live_delta = 0;
-            interaction_part<X>(p, t, (int)(tv >> 24), fx, o);
-            stepped = true;
-        }
-        if (!unlimited) {
-            const bool need = stepped && o.n == 2;
-            const unsigned m = __ballot_sync(0xFFFFFFFFu, need);
-            if (m) {
-                const int k = __popc(m);
-                const int leader = __ffs(m) - 1;
-                int got = 0;
-                if (lane == leader) {
-                    int old = atomicAdd(&p.cnt[cin].used, k);
-                    long long avail = spare - old;
-                    got = avail <= 0 ? 0 : (avail >= k ? k : (int)avail);
-                    if (got < k) atomicSub(&p.cnt[cin].used, k - got);
-                }
-                got = __shfl_sync(0xFFFFFFFFu, got, leader);
-                if (need && __popc(m & lanes_below) >= got) {
-                    // no room for the second output: discard the whole step
-                    load_track(qi, rsrc, t);
-                    copy_out(t, o);
-                    stepped = false;
+        for (int round = 0; round < kInteractRecords; ++round) {
+            const int pos = round * BS + tid;  // sorted position: a warp takes 32 consecutive ones
+            const bool mine = pos < n_here;
+            TrackReg<R> t;
+            Effects fx;
+            StepOut<R> o;
+            o.n = 0;
+            bool stepped = false;
+            long long rsrc = 0;
+            if (mine) {
+                const long long r = r0 + perm[pos];
+                const uint32_t tv = iq.tv[r];
+                t.x[0] = iq.x[r];
+                t.x[1] = iq.y[r];
+                t.x[2] = iq.z[r];
+                t.u[0] = iq.ux[r];
+                t.u[1] = iq.uy[r];
+                t.u[2] = iq.uz[r];
+                t.T = iq.T[r];
+                t.uid = iq.uid[r];
+                t.ev = iq.ev[r];
+                t.step = iq.step[r];
+                t.type = (int)(tv & 0xFFu);
+                t.vol = (int)((tv >> 8) & 0xFFFFu) - 2;
+                rsrc = iq.src[r];
+                fx.dep = iq.dep[r];
+                fx.esc = 0.0;
+                fx.kill = 0.0;
+                fx.col = score_col(p, t.vol, t.x[2]);
+                fx.finished = false;
+                fx.live_delta = 0;
+                interaction_part<X>(p, t, (int)(tv >> 24), fx, o);
+                stepped = true;
+            }
+            if (!unlimited) {
+                const bool need = stepped && o.n == 2;
+                const unsigned m = __ballot_sync(0xFFFFFFFFu, need);
+                if (m) {
+                    const int k = __popc(m);
+                    const int leader = __ffs(m) - 1;
+                    int got = 0;
+                    if (lane == leader) {
+                        int old = atomicAdd(&p.cnt[cin].used, k);
+                        long long avail = spare - old;
+                        got = avail <= 0 ? 0 : (avail >= k ? k : (int)avail);
+                        if (got < k) atomicSub(&p.cnt[cin].used, k - got);
+                    }
+                    got = __shfl_sync(0xFFFFFFFFu, got, leader);
+                    if (need && __popc(m & lanes_below) >= got) {
+                        // no room for the second output: discard the whole step
+                        load_track(qi, rsrc, t);
+                        copy_out(t, o);
+                        stepped = false;
+                    }
                 }
             }
-        }
-        if (stepped) apply_effects(p, t.ev, t.type, t.step, fx);
-        {
-            const unsigned md = __ballot_sync(0xFFFFFFFFu, mine && !stepped);
-            if (lane == 0 && md) {
-                atomicAdd(&p.total_steps[0], -(unsigned long long)__popc(md));
-                atomicAdd(&p.total_steps[1], (unsigned long long)__popc(md));
+            if (stepped) apply_effects(p, t.ev, t.type, t.step, fx);
+            {
+                const unsigned md = __ballot_sync(0xFFFFFFFFu, mine && !stepped);
+                if (lane == 0 && md) {
+                    atomicAdd(&p.total_steps[0], -(unsigned long long)__popc(md));
+                    atomicAdd(&p.total_steps[1], (unsigned long long)__popc(md));
+                }
             }
+            emit<2>(p, qo, co, lane, o, t.x, t.ev, t.vol, select ? s_eh : nullptr);
         }
-        emit<2>(p, qo, co, lane, o, t.x, t.ev, t.vol, select ? s_eh : nullptr);
         __syncthreads();
     }
     if constexpr (select) {
