@@ -105,6 +105,13 @@ typedef int32_t emt_status;
  *   sorted by model (needs one more buffer of slot_capacity records). */
 #define EMT_SCHEDULE_FUSED 0
 #define EMT_SCHEDULE_SPLIT 1
+/* PIPELINED: one kernel per step: its blocks first sample the interactions
+ * queued in the previous step (chunks sorted by model), then transport this
+ * step's tracks, so transport and sampling work overlap on the GPU; an
+ * interacting track's step completes one iteration later (no result
+ * changes; two queue buffers of slot_capacity records; no track selection
+ * or host spill). */
+#define EMT_SCHEDULE_PIPELINED 2
 
 typedef struct emt_ctx emt_ctx;
 
@@ -269,7 +276,14 @@ typedef struct emt_run_stats {
 } emt_run_stats;
 
 /* Step every track in flight until none is left or max_iterations
- * (<= 0: no limit) iterations have run.  stats may be NULL. */
+ * (<= 0: no limit) iterations have run.  stats may be NULL.  When the track
+ * slots cannot hold the next step (every track's step needs a second slot
+ * and none is free), half of the stored tracks move to host memory with
+ * their state and step counters and come back once fewer than a quarter of
+ * the slots are in use (the paper's buffering of tracks in CPU memory,
+ * Sec. 3.2); results do not change (stats.spilled counts those moves).
+ * EMT_ERR_CAPACITY remains only for a pipelined interaction queue that
+ * fills the slots by itself. */
 emt_status emt_run(emt_ctx* ctx, int32_t max_iterations, emt_run_stats* stats);
 
 /* Per-step diagnostics (Sec. 3.2, tracks in flight and time per step): as
@@ -388,7 +402,8 @@ emt_status emt_debug_wait_timeout(int32_t device, int32_t timeout_ms);
 emt_status emt_get_table(emt_ctx* ctx, int32_t m, int32_t p, int32_t q, double* out, int32_t cap, int32_t* n_out);
 
 /* Diagnostics: replace the tracks in flight by explicit track states and
- * read them back, to check single steps.  rec[n][10] = {type, T, x, y, z,
+ * read them back, to check single steps (fused or split schedule;
+ * EMT_ERR_BAD_STATE with the pipelined one).  rec[n][10] = {type, T, x, y, z,
  * ux, uy, uz, volume (-1 world vacuum), step}; uid[n]; event_slot[n]
  * indexes the events of the last submit.  host memory. */
 emt_status emt_debug_set_tracks(emt_ctx* ctx, int32_t n, const double* rec, const uint64_t* uid,

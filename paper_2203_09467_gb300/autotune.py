@@ -2,7 +2,9 @@
 
 The tunable knobs are the step schedule (fused: one kernel regrouping the
 interactions inside each block; split: a transport kernel and an
-interaction kernel joined by a queue in device memory), the block size (128
+interaction kernel joined by a queue in device memory; pipelined: one
+kernel per step that samples the previous step's queue while it transports
+the current tracks), the block size (128
 or 256 threads: a larger block regroups more interacting tracks per model, a
 smaller one leaves more blocks per SM) and the step-loop driver (a host loop
 with one counter read per step, CUDA graphs of 12 or 24 steps with one
@@ -24,7 +26,7 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_autotune_cach
 
 CANDIDATES = [
     {"block_size": b, "loop_mode": loop, "graph_steps": k, "schedule": sched}
-    for sched in ("fused", "split")
+    for sched in ("fused", "split", "pipelined")
     for b in (128, 256)
     for loop, k in (("plain", 12), ("graph", 12), ("graph", 24))
 ] + [

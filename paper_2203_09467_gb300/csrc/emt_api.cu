@@ -48,7 +48,8 @@ struct Plan {
     size_t zb, lmat, lbin;
     size_t st_ev, st_type, st_T, st_pos, st_dir, st_uid, st_slot, st_ids, st_start, st_runs;
     size_t slots_tmp, out_hist, out_summary;
-    size_t iq[13];  // split schedule: interaction queue fields
+    size_t iq[13];      // split schedule: interaction queue fields
+    size_t iq_alt[13];  // pipelined schedule: the second queue
     size_t skey, sperm;  // split schedule: scheduling classes and order of charged tracks in a field
     size_t step_hist;  // [3][step_bins] when step_bins > 0
     int step_bins;
@@ -58,7 +59,8 @@ struct Plan {
     int64_t Q;
     int max_events, hstride, max_prim;
     bool mixed;
-    bool split;
+    bool split;      // a queue of interacting tracks (split or pipelined schedule)
+    bool pipelined;  // one kernel per step, interactions sampled one iteration later
 };
 
 Plan make_plan(const emt_options& o)
@@ -121,11 +123,15 @@ Plan make_plan(const emt_options& o)
     p.st_start = p.add(E * 4);
     p.st_runs = p.add(E * 4);
     p.slots_tmp = p.add(E * 4);
-    p.split = o.schedule == EMT_SCHEDULE_SPLIT;
+    p.split = o.schedule == EMT_SCHEDULE_SPLIT || o.schedule == EMT_SCHEDULE_PIPELINED;
+    p.pipelined = o.schedule == EMT_SCHEDULE_PIPELINED;
+    for (int f = 0; f < 13; ++f) p.iq_alt[f] = 0;
     if (p.split) {
         // x y z ux uy uz T uid dep ev step tv src
         const size_t iqs[13] = {8, 8, 8, rs, rs, rs, rs, 8, 8, 4, 4, 4, 4};
         for (int f = 0; f < 13; ++f) p.iq[f] = p.add(Q * iqs[f]);
+        if (p.pipelined)
+            for (int f = 0; f < 13; ++f) p.iq_alt[f] = p.add(Q * iqs[f]);
         p.skey = p.add(Q);
         p.sperm = p.add(Q * 4);
     } else {
@@ -154,7 +160,8 @@ bool valid_options(const emt_options& o, std::string& why)
         return why = "loop_mode", false;
     if (o.loop_mode == EMT_LOOP_PERSISTENT && o.graph_steps <= 0)
         return why = "graph_steps (steps per persistent launch) must be positive", false;
-    if (o.schedule != EMT_SCHEDULE_FUSED && o.schedule != EMT_SCHEDULE_SPLIT) return why = "schedule", false;
+    if (o.schedule != EMT_SCHEDULE_FUSED && o.schedule != EMT_SCHEDULE_SPLIT && o.schedule != EMT_SCHEDULE_PIPELINED)
+        return why = "schedule", false;
     if (o.loop_mode == EMT_LOOP_GRAPH && (o.graph_steps <= 0 || o.graph_steps % 6 != 0))
         return why = "graph_steps must be a positive multiple of 6", false;
     if (o.step_hist_bins < 0 || o.step_hist_bins > (1 << 20)) return why = "step_hist_bins out of [0, 2^20]", false;
@@ -248,9 +255,11 @@ struct emt_ctx {
     Params<float> pf;
     int64_t it = 0;  // step-loop iterations so far
     int64_t live_g = 0, live_c = 0;
+    int64_t live_q = 0;  // pipelined schedule: interactions queued for the next iteration
     int resident_blocks = 0;
     int resident_a = 0, resident_b = 0;  // split schedule: transport, interaction kernels
     int persist_grid = 0;                // persistent step loop: resident blocks of the cooperative launch
+    int resident_p = 0;                  // pipelined schedule: resident blocks of the step kernel
     long long wait_cycles = 0;           // bound of one grid-barrier wait, SM clock cycles
     int block = 128;
     // host event table
@@ -277,6 +286,13 @@ struct emt_ctx {
     // field of the track layout (the most recently spilled at the end)
     std::vector<char> spill_store[11];
     int64_t spill_n = 0;
+    // tracks moved to host memory when the track slots could not hold the
+    // next step (photons, charged): field arrays of over_n[r] records
+    std::vector<char> over_store[2][11];
+    int64_t over_n[2] = {0, 0};
+    // pipelined schedule: queued interactions moved to host memory likewise
+    std::vector<char> overq_store[13];
+    int64_t overq_n = 0;
     // per-step records of emt_run_traced (null otherwise)
     emt_step_record* trace = nullptr;
     int32_t trace_cap = 0, trace_n = 0;
@@ -285,6 +301,12 @@ struct emt_ctx {
     T* at(size_t off) const { return reinterpret_cast<T*>(pool + off); }
     bool mixed() const { return plan.mixed; }
 };
+
+// tracks still to be stepped: in the track buffers, and (pipelined
+// schedule) with an interaction queued for the next iteration
+int64_t in_flight(const emt_ctx* c) { return c->live_g + c->live_c + c->live_q; }
+// tracks waiting in host memory (host spill and slot overflow)
+int64_t on_host(const emt_ctx* c) { return c->spill_n + c->over_n[0] + c->over_n[1] + c->overq_n; }
 
 namespace {
 
@@ -337,21 +359,24 @@ void fill_common(emt_ctx* c, Params<R>& p)
 {
     const Plan& pl = c->plan;
     fill_tracks(c, p);
+    auto fill_queue = [&](InterQueue<R>& q, const size_t* o) {
+        q.x = c->at<double>(o[0]);
+        q.y = c->at<double>(o[1]);
+        q.z = c->at<double>(o[2]);
+        q.ux = c->at<R>(o[3]);
+        q.uy = c->at<R>(o[4]);
+        q.uz = c->at<R>(o[5]);
+        q.T = c->at<R>(o[6]);
+        q.uid = c->at<uint64_t>(o[7]);
+        q.dep = c->at<double>(o[8]);
+        q.ev = c->at<uint32_t>(o[9]);
+        q.step = c->at<uint32_t>(o[10]);
+        q.tv = c->at<uint32_t>(o[11]);
+        q.src = c->at<uint32_t>(o[12]);
+    };
     if (pl.split) {
-        InterQueue<R>& q = p.iq;
-        q.x = c->at<double>(pl.iq[0]);
-        q.y = c->at<double>(pl.iq[1]);
-        q.z = c->at<double>(pl.iq[2]);
-        q.ux = c->at<R>(pl.iq[3]);
-        q.uy = c->at<R>(pl.iq[4]);
-        q.uz = c->at<R>(pl.iq[5]);
-        q.T = c->at<R>(pl.iq[6]);
-        q.uid = c->at<uint64_t>(pl.iq[7]);
-        q.dep = c->at<double>(pl.iq[8]);
-        q.ev = c->at<uint32_t>(pl.iq[9]);
-        q.step = c->at<uint32_t>(pl.iq[10]);
-        q.tv = c->at<uint32_t>(pl.iq[11]);
-        q.src = c->at<uint32_t>(pl.iq[12]);
+        fill_queue(p.iq, pl.iq);
+        if (pl.pipelined) fill_queue(p.iq_alt, pl.iq_alt);
         p.skey = c->at<uint8_t>(pl.skey);
         p.sperm = c->at<uint32_t>(pl.sperm);
     }
@@ -504,7 +529,8 @@ template <typename R>
 int launches_per_step(const emt_ctx* c, const Params<R>& p)
 {
     if (!c->plan.split) return 1;
-    return 2 + ((p.has_field && p.max_active <= 0) ? 2 : 0);
+    const int sort = (p.has_field && p.max_active <= 0) ? 2 : 0;
+    return (c->plan.pipelined ? 1 : 2) + sort;
 }
 
 template <typename R>
@@ -518,7 +544,7 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
     const unsigned long long steps0 = c->steps_seen[0], def0 = c->steps_seen[1], held0 = c->steps_seen[2],
                              sub0 = c->steps_seen[3];
     unsigned long long last_steps = steps0;
-    const int64_t live0 = c->live_g + c->live_c;
+    const int64_t live0 = in_flight(c);
     int64_t peak = live0;
     double kernel_ms = 0.0;
     unsigned long long deferred_prev = def0, held_prev = held0;
@@ -567,6 +593,111 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
         s.peak_spilled = std::max<int64_t>(s.peak_spilled, c->spill_n);
         return EMT_OK;
     };
+    // Slot overflow: every track's next step needs a second output slot and
+    // none is free (a deterministic step repeats identically, so waiting
+    // cannot help).  Half of each particle region, the tracks next to its
+    // free end, moves to host memory with its state and step counter; they
+    // come back when the device holds fewer than Q/4 tracks.  Results do not
+    // change (each track's random stream is keyed on its own steps).
+    // pipelined schedule: the queue that the next iteration samples, its
+    // field sizes and its count (slot cs)
+    const size_t qfs[13] = {8, 8, 8, rs, rs, rs, rs, 8, 8, 4, 4, 4, 4};
+    auto pending_queue = [&](int64_t it) { return (it & 1) ? pl.iq : pl.iq_alt; };
+    auto overflow_out = [&]() -> emt_status {
+        const int side = (int)(c->it & 1), cs = (int)(c->it % 3);
+        const int64_t nG = c->live_g, nC = c->live_c;
+        const int64_t k[2] = {nG / 2, nC / 2};
+        const int64_t kq = c->live_q / 2;
+        if (k[0] + k[1] + kq == 0)
+            return fail(c, EMT_ERR_CAPACITY, "no track could advance: slot_capacity is too small");
+        if (kq > 0) {
+            // the last kq records of the pending queue
+            const size_t* qo = pending_queue(c->it);
+            const int64_t nq = c->live_q;
+            for (int f = 0; f < 13; ++f) {
+                std::vector<char>& v = c->overq_store[f];
+                const size_t old = v.size();
+                v.resize(old + qfs[f] * kq);
+                EMT_CUDA(c, cudaMemcpyAsync(v.data() + old, c->pool + qo[f] + qfs[f] * (nq - kq), qfs[f] * kq,
+                                            cudaMemcpyDeviceToHost, c->stream));
+            }
+            const int nq2 = (int)(nq - kq);
+            EMT_CUDA(c, cudaMemcpyAsync(c->pool + pl.cnt + sizeof(Counters) * cs + offsetof(Counters, n_int), &nq2,
+                                        sizeof nq2, cudaMemcpyHostToDevice, c->stream));
+            EMT_CUDA(c, cudaStreamSynchronize(c->stream));
+            c->overq_n += kq;
+            c->live_q = nq2;
+            s.spilled += kq;
+            s.peak_spilled = std::max<int64_t>(s.peak_spilled, on_host(c));
+        }
+        const int64_t first[2] = {nG - k[0], pl.Q - nC};  // photons: top of [0, nG); charged: bottom of [Q-nC, Q)
+        for (int r = 0; r < 2; ++r) {
+            if (k[r] == 0) continue;
+            for (int f = 0; f < 11; ++f) {
+                std::vector<char>& v = c->over_store[r][f];
+                const size_t old = v.size();
+                v.resize(old + fs[f] * k[r]);
+                EMT_CUDA(c, cudaMemcpyAsync(v.data() + old, c->pool + pl.trk[side][f] + fs[f] * first[r],
+                                            fs[f] * k[r], cudaMemcpyDeviceToHost, c->stream));
+            }
+            c->over_n[r] += k[r];
+        }
+        int n2[2] = {(int)(nG - k[0]), (int)(nC - k[1])};
+        EMT_CUDA(c, cudaMemcpyAsync(c->pool + pl.cnt + sizeof(Counters) * cs + offsetof(Counters, n), n2, sizeof n2,
+                                    cudaMemcpyHostToDevice, c->stream));
+        EMT_CUDA(c, cudaStreamSynchronize(c->stream));
+        c->live_g = n2[0];
+        c->live_c = n2[1];
+        s.spilled += k[0] + k[1];
+        s.peak_spilled = std::max<int64_t>(s.peak_spilled, on_host(c));
+        return EMT_OK;
+    };
+    auto overflow_in = [&]() -> emt_status {
+        const int64_t N = in_flight(c);
+        if (c->over_n[0] + c->over_n[1] + c->overq_n == 0 || N >= pl.Q / 4) return EMT_OK;
+        int64_t budget = pl.Q / 2 - N;
+        const int side = (int)(c->it & 1), cs = (int)(c->it % 3);
+        if (c->overq_n > 0) {
+            // queued interactions back to the end of the pending queue
+            const int64_t k = std::min<int64_t>(c->overq_n, budget);
+            const int64_t from = c->overq_n - k;
+            const size_t* qo = pending_queue(c->it);
+            for (int f = 0; f < 13; ++f)
+                EMT_CUDA(c, cudaMemcpyAsync(c->pool + qo[f] + qfs[f] * c->live_q, c->overq_store[f].data() + qfs[f] * from,
+                                            qfs[f] * k, cudaMemcpyHostToDevice, c->stream));
+            const int nq2 = (int)(c->live_q + k);
+            EMT_CUDA(c, cudaMemcpyAsync(c->pool + pl.cnt + sizeof(Counters) * cs + offsetof(Counters, n_int), &nq2,
+                                        sizeof nq2, cudaMemcpyHostToDevice, c->stream));
+            EMT_CUDA(c, cudaStreamSynchronize(c->stream));
+            for (int f = 0; f < 13; ++f) c->overq_store[f].resize(qfs[f] * from);
+            c->overq_n = from;
+            c->live_q = nq2;
+            budget -= k;
+        }
+        int64_t cnt2[2] = {c->live_g, c->live_c};
+        for (int r = 0; r < 2 && budget > 0; ++r) {
+            const int64_t k = std::min<int64_t>(c->over_n[r], budget);
+            if (k <= 0) continue;
+            const int64_t from = c->over_n[r] - k;  // the most recently moved out
+            const int64_t to = r == 0 ? cnt2[0] : pl.Q - cnt2[1] - k;
+            for (int f = 0; f < 11; ++f)
+                EMT_CUDA(c, cudaMemcpyAsync(c->pool + pl.trk[side][f] + fs[f] * to,
+                                            c->over_store[r][f].data() + fs[f] * from, fs[f] * k,
+                                            cudaMemcpyHostToDevice, c->stream));
+            EMT_CUDA(c, cudaStreamSynchronize(c->stream));
+            for (int f = 0; f < 11; ++f) c->over_store[r][f].resize(fs[f] * from);
+            c->over_n[r] = from;
+            cnt2[r] += k;
+            budget -= k;
+        }
+        int n2[2] = {(int)cnt2[0], (int)cnt2[1]};
+        EMT_CUDA(c, cudaMemcpyAsync(c->pool + pl.cnt + sizeof(Counters) * cs + offsetof(Counters, n), n2, sizeof n2,
+                                    cudaMemcpyHostToDevice, c->stream));
+        EMT_CUDA(c, cudaStreamSynchronize(c->stream));
+        c->live_g = n2[0];
+        c->live_c = n2[1];
+        return EMT_OK;
+    };
     auto read_counts = [&]() -> emt_status {
         EMT_CUDA(c, cudaMemcpyAsync(c->h_cnt, c->pool + pl.cnt + sizeof(Counters) * (c->it % 3), sizeof(Counters),
                                     cudaMemcpyDeviceToHost, c->stream));
@@ -574,17 +705,20 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
         float ms = 0.f;
         EMT_CUDA(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
         kernel_ms += ms;
-        const bool same = c->live_g == c->h_cnt->n[0] && c->live_c == c->h_cnt->n[1];
+        const int64_t q = pl.pipelined ? (int64_t)c->h_cnt->n_int : 0;
+        const bool same = c->live_g == c->h_cnt->n[0] && c->live_c == c->h_cnt->n[1] && c->live_q == q;
         c->live_g = c->h_cnt->n[0];
         c->live_c = c->h_cnt->n[1];
-        peak = std::max<int64_t>(peak, c->live_g + c->live_c);
-        if (same && c->live_g + c->live_c > 0) {
+        c->live_q = q;
+        peak = std::max<int64_t>(peak, in_flight(c));
+        if (same && in_flight(c) > 0) {
             // unchanged population: make sure some track advanced
             EMT_CUDA(c, cudaMemcpyAsync(c->h_steps, c->pool + pl.total_steps, 16, cudaMemcpyDeviceToHost, c->stream));
             EMT_CUDA(c, cudaStreamSynchronize(c->stream));
-            if (c->h_steps[0] == last_steps)
-                return fail(c, EMT_ERR_CAPACITY,
-                            "no track could advance: slot_capacity is too small for the tracks in flight");
+            if (c->h_steps[0] == last_steps) {
+                emt_status r = overflow_out();
+                if (r != EMT_OK) return r;
+            }
             last_steps = c->h_steps[0];
         }
         return EMT_OK;
@@ -594,13 +728,19 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
             emt_status r0 = refill();
             if (r0 != EMT_OK) return r0;
         }
+        {
+            emt_status r0 = overflow_in();
+            if (r0 != EMT_OK) return r0;
+        }
         int side = (int)(c->it & 1), cin = (int)(c->it % 3), cout = (int)((c->it + 1) % 3),
             cclr = (int)((c->it + 2) % 3);
         int64_t chunks = (c->live_g + c->block - 1) / c->block + (c->live_c + c->block - 1) / c->block;
         int grid = (int)std::max<int64_t>(1, std::min<int64_t>(chunks, c->resident_blocks));
         EMT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
         cudaError_t e =
-            c->plan.split
+            c->plan.pipelined
+                ? Launch<R>::step_pipe(p, side, cin, cout, cclr, c->resident_p, c->resident_b, c->block, c->stream)
+            : c->plan.split
                 ? Launch<R>::step_split(p, side, cin, cout, cclr,
                                         (int)std::max<int64_t>(1, std::min<int64_t>(chunks, c->resident_a)),
                                         c->resident_b, c->block, c->stream)
@@ -634,7 +774,7 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
     int64_t done_it = 0;
     auto budget_left = [&]() { return max_iterations <= 0 || done_it < max_iterations; };
     if (c->opt.loop_mode == EMT_LOOP_PLAIN || c->trace || pl.spill_on) {
-        while ((c->live_g + c->live_c > 0 || c->spill_n > 0) && budget_left()) {
+        while ((in_flight(c) > 0 || on_host(c) > 0) && budget_left()) {
             emt_status r = one_plain();
             if (r != EMT_OK) return r;
             ++done_it;
@@ -643,9 +783,13 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
         // up to graph_steps steps per cooperative launch; the launch ends
         // early when no track is left and reports how many steps it ran
         GridSync* gs = c->at<GridSync>(pl.gsync);
-        while (c->live_g + c->live_c > 0 && budget_left()) {
+        while ((in_flight(c) > 0 || on_host(c) > 0) && budget_left()) {
             const int k = max_iterations > 0 ? (int)std::min<int64_t>(c->opt.graph_steps, max_iterations - done_it)
                                              : c->opt.graph_steps;
+            {
+                emt_status r0 = overflow_in();
+                if (r0 != EMT_OK) return r0;
+            }
             EMT_CUDA(c, cudaMemsetAsync(gs, 0, sizeof(GridSync), c->stream));
             EMT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
             cudaError_t e = Launch<R>::persist(p, c->it, k, gs, c->wait_cycles, c->persist_grid, c->block, c->stream);
@@ -671,7 +815,7 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
         }
     } else {
         const int K = c->opt.graph_steps;
-        while (c->live_g + c->live_c > 0 && budget_left()) {
+        while ((in_flight(c) > 0 || on_host(c) > 0) && budget_left()) {
             if (c->it % 6 != 0 || (max_iterations > 0 && max_iterations - done_it < K)) {
                 emt_status r = one_plain();
                 if (r != EMT_OK) return r;
@@ -683,7 +827,10 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
                 EMT_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
                 for (int k = 0; k < K; ++k) {
                     int side = k & 1, cin = k % 3, cout = (k + 1) % 3, cclr = (k + 2) % 3;
-                    cudaError_t e = c->plan.split ? Launch<R>::step_split(p, side, cin, cout, cclr, c->resident_a,
+                    cudaError_t e = c->plan.pipelined
+                                        ? Launch<R>::step_pipe(p, side, cin, cout, cclr, c->resident_p, c->resident_b,
+                                                               c->block, c->stream)
+                                    : c->plan.split ? Launch<R>::step_split(p, side, cin, cout, cclr, c->resident_a,
                                                                           c->resident_b, c->block, c->stream)
                                                   : Launch<R>::step(p, side, cin, cout, cclr, c->resident_blocks,
                                                                     c->block, c->stream);
@@ -695,6 +842,10 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
                 EMT_CUDA(c, cudaStreamEndCapture(c->stream, &g));
                 EMT_CUDA(c, cudaGraphInstantiate(&c->graph, g, 0));
                 cudaGraphDestroy(g);
+            }
+            {
+                emt_status r0 = overflow_in();
+                if (r0 != EMT_OK) return r0;
             }
             EMT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
             EMT_CUDA(c, cudaGraphLaunch(c->graph, c->stream));
@@ -728,7 +879,7 @@ emt_status run_loop(emt_ctx* c, int32_t max_iterations, emt_run_stats* st)
     s.held = (int64_t)(c->steps_seen[2] - held0);
     s.rk4_substeps = (int64_t)(c->steps_seen[3] - sub0);
     s.peak_tracks = peak;
-    s.live_tracks = c->live_g + c->live_c + c->spill_n;
+    s.live_tracks = in_flight(c) + on_host(c);
     s.kernel_ms = kernel_ms;
     // every launch reads its inputs and writes its outputs once; the
     // outputs of one launch are the inputs of the next
@@ -870,6 +1021,9 @@ emt_status emt_create(const emt_options* o, emt_ctx** out)
         };
         c->resident_a = std::max(1, dev_sms * blocks(0));
         c->resident_b = std::max(1, dev_sms * blocks(1));
+        if (c->plan.pipelined)
+            c->resident_p = std::max(1, dev_sms * (c->mixed() ? Launch<float>::max_blocks_pipe(c->block)
+                                                              : Launch<double>::max_blocks_pipe(c->block)));
     }
     if (o->loop_mode == EMT_LOOP_PERSISTENT) {
         int coop = 0, clock_khz = 0;
@@ -1034,7 +1188,7 @@ static emt_status submit_impl(emt_ctx* c, int32_t n_events, const uint64_t* ids,
     const int n = pr->n;
     if ((int64_t)n > pl.max_prim) return fail(c, EMT_ERR_CAPACITY, "too many primaries in one submit");
     if ((int64_t)c->free_slots.size() < n_events) return fail(c, EMT_ERR_CAPACITY, "no free event slots");
-    if (c->live_g + c->live_c + n > pl.Q - 2) return fail(c, EMT_ERR_CAPACITY, "no free track slots");
+    if (in_flight(c) + n > pl.Q - 2) return fail(c, EMT_ERR_CAPACITY, "no free track slots");
     for (int e = 0; e < n_events; ++e)
         if (c->id_to_slot.count(ids[e])) return fail(c, EMT_ERR_INVALID_ARG, "event id already in flight");
     {
@@ -1241,7 +1395,7 @@ emt_status emt_read_all(emt_ctx* c, double* hist, double* summary, uint64_t* ids
 {
     emt_status r = check_ready(c);
     if (r != EMT_OK) return r;
-    if (c->live_g + c->live_c + c->spill_n != 0) return fail(c, EMT_ERR_NOT_READY, "tracks still in flight");
+    if (in_flight(c) + on_host(c) != 0) return fail(c, EMT_ERR_NOT_READY, "tracks still in flight");
     if (where != EMT_HOST && where != EMT_DEVICE) return fail(c, EMT_ERR_INVALID_ARG, "where");
     const Plan& pl = c->plan;
     int n = (int)c->order.size();
@@ -1273,7 +1427,7 @@ emt_status emt_read_all(emt_ctx* c, double* hist, double* summary, uint64_t* ids
 
 int32_t emt_events_in_flight(const emt_ctx* c) { return c ? (int32_t)c->order.size() : 0; }
 
-int64_t emt_tracks_in_flight(const emt_ctx* c) { return c ? c->live_g + c->live_c + c->spill_n : 0; }
+int64_t emt_tracks_in_flight(const emt_ctx* c) { return c ? in_flight(c) + on_host(c) : 0; }
 
 emt_status emt_get_table(emt_ctx* c, int32_t m, int32_t p, int32_t q, double* out, int32_t cap, int32_t* n_out)
 {
@@ -1303,6 +1457,7 @@ emt_status emt_debug_set_tracks(emt_ctx* c, int32_t n, const double* rec, const 
     emt_status r = check_ready(c);
     if (r != EMT_OK) return r;
     if (n < 0 || (n > 0 && (!rec || !uid || !slot))) return fail(c, EMT_ERR_INVALID_ARG, "bad arguments");
+    if (c->plan.pipelined) return fail(c, EMT_ERR_BAD_STATE, "explicit track states need the fused or split schedule");
     if (n > c->plan.Q / 2) return fail(c, EMT_ERR_CAPACITY, "too many tracks");
     for (int i = 0; i < n; ++i) {
         int t = (int)rec[10 * (size_t)i], v = (int)rec[10 * (size_t)i + 8];
@@ -1345,6 +1500,7 @@ emt_status emt_debug_get_tracks(emt_ctx* c, int32_t cap, double* rec, uint64_t* 
     emt_status r = check_ready(c);
     if (r != EMT_OK) return r;
     if (!n_out) return fail(c, EMT_ERR_INVALID_ARG, "null n_out");
+    if (c->plan.pipelined) return fail(c, EMT_ERR_BAD_STATE, "explicit track states need the fused or split schedule");
     int n = (int)(c->live_g + c->live_c);
     *n_out = n;
     if (n == 0) return EMT_OK;

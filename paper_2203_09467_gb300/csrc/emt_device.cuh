@@ -225,7 +225,8 @@ struct Params {
     long long Q;
     Counters* cnt;  // [3]
     int* status;
-    InterQueue<R> iq;  // split schedule only
+    InterQueue<R> iq;      // split and pipelined schedules
+    InterQueue<R> iq_alt;  // pipelined schedule: the second queue (iterations alternate)
     // split schedule in a field: scheduling class of each charged input
     // track (skey[i], i = index in the charged region) and the order in
     // which the transport kernel takes them (sperm: indices, most

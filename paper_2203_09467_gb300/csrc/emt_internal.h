@@ -56,6 +56,11 @@ struct Launch {
     static cudaError_t step_split(const Params<R>& p, int side, int cin, int cout, int cclr, int grid_a, int grid_b,
                                   int block, cudaStream_t st);
     static int max_blocks_split(int block, int which);
+    // pipelined schedule: one kernel per step (plus the two sorting launches
+    // of the charged tracks in a field, on grid_sort blocks)
+    static cudaError_t step_pipe(const Params<R>& p, int side, int cin, int cout, int cclr, int grid, int grid_sort,
+                                 int block, cudaStream_t st);
+    static int max_blocks_pipe(int block);
     // host spill: append n tracks of the spill buffer to side `side`
     static cudaError_t unspill(const Params<R>& p, int side, int cs, int n, cudaStream_t st);
     // persistent step loop (fused schedule, cooperative launch of `grid`

@@ -255,4 +255,64 @@ int Launch<R>::max_blocks_split(int block, int which)
     return block == 128 ? min_blocks_split<R, 128>(which) : min_blocks_split<R, 256>(which);
 }
 
+template <typename R, int BS, bool X>
+static void launch_pipe_x(const Params<R>& p, int side, int cin, int cout, int cclr, int grid, int grid_sort,
+                          cudaStream_t st)
+{
+    if (p.has_field) {
+        k_sort_keys<R><<<grid_sort, 256, 0, st>>>(p, side, cin);
+        k_sort_order<R><<<grid_sort, 256, 0, st>>>(p, cin);
+    }
+    if (p.geom == kGeomCylinders)
+        k_pipe<R, BS, kGeomCylinders, X><<<grid, BS, 0, st>>>(p, side, cin, cout, cclr);
+    else
+        k_pipe<R, BS, kGeomLayers, X><<<grid, BS, 0, st>>>(p, side, cin, cout, cclr);
+}
+
+template <typename R>
+cudaError_t Launch<R>::step_pipe(const Params<R>& p, int side, int cin, int cout, int cclr, int grid, int grid_sort,
+                                 int block, cudaStream_t st)
+{
+    const bool x = extended(p);
+    if (block == 128) {
+        if (x)
+            launch_pipe_x<R, 128, true>(p, side, cin, cout, cclr, grid, grid_sort, st);
+        else
+            launch_pipe_x<R, 128, false>(p, side, cin, cout, cclr, grid, grid_sort, st);
+    } else if (block == 256) {
+        if (x)
+            launch_pipe_x<R, 256, true>(p, side, cin, cout, cclr, grid, grid_sort, st);
+        else
+            launch_pipe_x<R, 256, false>(p, side, cin, cout, cclr, grid, grid_sort, st);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// resident blocks per SM of the pipelined kernel, the smallest over its
+// instantiations
+template <typename R, int BS>
+static int min_blocks_pipe()
+{
+    int n[4] = {0, 0, 0, 0};
+    cudaError_t e[4];
+    e[0] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[0], k_pipe<R, BS, kGeomLayers, false>, BS, 0);
+    e[1] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[1], k_pipe<R, BS, kGeomCylinders, false>, BS, 0);
+    e[2] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[2], k_pipe<R, BS, kGeomLayers, true>, BS, 0);
+    e[3] = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n[3], k_pipe<R, BS, kGeomCylinders, true>, BS, 0);
+    int m = 1 << 30;
+    for (int k = 0; k < 4; ++k) {
+        if (e[k] != cudaSuccess) return 1;
+        if (n[k] < m) m = n[k];
+    }
+    return m > 0 ? m : 1;
+}
+
+template <typename R>
+int Launch<R>::max_blocks_pipe(int block)
+{
+    return block == 128 ? min_blocks_pipe<R, 128>() : min_blocks_pipe<R, 256>();
+}
+
 }  // namespace emt

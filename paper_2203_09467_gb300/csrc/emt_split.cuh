@@ -40,11 +40,13 @@ constexpr int transport_threads_per_sm()
 // Phase A of one track in the transport kernel (every lane of the warp
 // calls it; `active` lanes hold a track in t, `held` ones are copied
 // unchanged): transport, survivor output, and the queueing of an
-// interacting track for the interaction kernel.
+// interacting track (into iq, counted in *n_iq) for the interaction phase.
+// count_queued: a queued track's step is counted now (split schedule) or
+// when its interaction is committed (pipelined schedule).
 template <int G, bool X, typename R>
-__device__ __forceinline__ void transport_lane(const Params<R>& p, const Tracks<R>& qo, Counters* co, int cin,
-                                               int lane, TrackReg<R>& t, bool active, bool held, long long src,
-                                               unsigned* eh)
+__device__ __forceinline__ void transport_lane(const Params<R>& p, const Tracks<R>& qo, Counters* co,
+                                               const InterQueue<R>& iq, int* n_iq, bool count_queued, int lane,
+                                               TrackReg<R>& t, bool active, bool held, long long src, unsigned* eh)
 {
     const unsigned lanes_below = (1u << lane) - 1u;
     Effects fx;
@@ -65,7 +67,7 @@ __device__ __forceinline__ void transport_lane(const Params<R>& p, const Tracks<
     }
     count_substeps(p, lane, substeps);
     {
-        const unsigned ms = __ballot_sync(0xFFFFFFFFu, active && !held);
+        const unsigned ms = __ballot_sync(0xFFFFFFFFu, active && !held && (count_queued || model == kNoInteraction));
         if (lane == 0 && ms) atomicAdd(&p.total_steps[0], (unsigned long long)__popc(ms));
     }
     emit<1>(p, qo, co, lane, o, t.x, t.ev, t.vol, eh);
@@ -74,11 +76,10 @@ __device__ __forceinline__ void transport_lane(const Params<R>& p, const Tracks<
     const unsigned m = __ballot_sync(0xFFFFFFFFu, need);
     if (m) {
         int base = 0;
-        if (lane == 0) base = atomicAdd(&p.cnt[cin].n_int, __popc(m));
+        if (lane == 0) base = atomicAdd(n_iq, __popc(m));
         base = __shfl_sync(0xFFFFFFFFu, base, 0);
         if (need) {
             const long long k = (long long)base + __popc(m & lanes_below);
-            const InterQueue<R>& iq = p.iq;
             if (k < p.Q) {
                 iq.x[k] = t.x[0];
                 iq.y[k] = t.x[1];
@@ -215,7 +216,7 @@ __global__ void __launch_bounds__(BS, transport_threads_per_sm<R>() / BS)
             const long long src = photon_chunk ? i : Q - nC + i;
             TrackReg<R> t;
             if (active) load_track(qi, src, t);
-            transport_lane<G, X>(p, qo, co, cin, lane, t, active, false, src, nullptr);
+            transport_lane<G, X>(p, qo, co, p.iq, &p.cnt[cin].n_int, true, lane, t, active, false, src, nullptr);
         }
         return;
     }
@@ -307,7 +308,7 @@ __global__ void __launch_bounds__(BS, transport_threads_per_sm<R>() / BS)
             const unsigned mh = __ballot_sync(0xFFFFFFFFu, held);
             if (lane == 0 && mh) atomicAdd(&p.total_steps[2], (unsigned long long)__popc(mh));
         }
-        transport_lane<G, X>(p, qo, co, cin, lane, t, active, held, src, s_eh);
+        transport_lane<G, X>(p, qo, co, p.iq, &p.cnt[cin].n_int, true, lane, t, active, held, src, s_eh);
     }
     if constexpr (select) {
         __syncthreads();
@@ -322,34 +323,47 @@ __global__ void __launch_bounds__(BS, transport_threads_per_sm<R>() / BS)
 // chunks give warps of fewer models.
 constexpr int kInteractRecords = 2;
 
-template <typename R, int BS, bool S, bool X>
-__global__ void __launch_bounds__(BS, 512 / BS) k_interact(Params<R> p, int side, int cin, int cout)
+// copy queue record r of `from` to record k of `to`
+template <typename R>
+__device__ __forceinline__ void copy_record(const InterQueue<R>& from, long long r, const InterQueue<R>& to, long long k)
+{
+    to.x[k] = from.x[r];
+    to.y[k] = from.y[r];
+    to.z[k] = from.z[r];
+    to.ux[k] = from.ux[r];
+    to.uy[k] = from.uy[r];
+    to.uz[k] = from.uz[r];
+    to.T[k] = from.T[r];
+    to.uid[k] = from.uid[r];
+    to.dep[k] = from.dep[r];
+    to.ev[k] = from.ev[r];
+    to.step[k] = from.step[r];
+    to.tv[k] = from.tv[r];
+    to.src[k] = from.src[r];
+}
+
+// The interaction phase over the n_int records of queue iq: chunks of
+// kInteractRecords * BS records, each counting-sorted by model in shared
+// memory and sampled by the block's warps in sorted order.  A record whose
+// step makes two outputs needs a growth token from the `spare` slots; a
+// step without one is deferred: split schedule (kPipe false): the track is
+// copied unchanged from the input buffer qi (it repeats the whole step);
+// pipelined schedule: the record is queued again, unchanged, in qnext
+// (counted in *n_next), and its interaction is sampled in the next
+// iteration.  Either way it keeps its step counter, so no result changes.
+// Every thread of the block calls it (barriers).
+template <typename R, int BS, bool X, bool kPipe>
+__device__ __forceinline__ void interact_chunks(const Params<R>& p, const Tracks<R>& qi, const Tracks<R>& qo,
+                                                Counters* co, int cin, const InterQueue<R>& iq, int n_int,
+                                                long long spare, bool unlimited, const InterQueue<R>& qnext,
+                                                int* n_next, unsigned* eh, int& s_chunk, int* count, int* offset,
+                                                unsigned short* perm)
 {
     constexpr int CH = BS * kInteractRecords;
-    __shared__ int s_chunk;
-    __shared__ int count[kNumModels];
-    __shared__ int offset[kNumModels + 1];
-    __shared__ unsigned short perm[CH];
-    __shared__ unsigned s_eh[S ? kEBins : 1];
-    constexpr bool select = S;
-    if constexpr (select) {
-        for (int b = threadIdx.x; b < kEBins; b += BS) s_eh[b] = 0u;
-        __syncthreads();
-    }
-    const Tracks<R> qi = p.q[side];
-    const Tracks<R> qo = p.q[side ^ 1];
-    const long long Q = p.Q;
-    const long long ntot = (long long)p.cnt[cin].n[0] + p.cnt[cin].n[1];
-    const long long spare = Q - ntot;
-    const bool unlimited = 2 * ntot <= Q;
-    const int n_int = p.cnt[cin].n_int;
     const int chunks = (n_int + CH - 1) / CH;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const unsigned lanes_below = (1u << lane) - 1u;
-    Counters* const co = &p.cnt[cout];
-    const InterQueue<R> iq = p.iq;
-
     for (;;) {
         if (tid == 0) s_chunk = atomicAdd(&p.cnt[cin].work_b, 1);
         if (tid < kNumModels) count[tid] = 0;
@@ -394,8 +408,9 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_interact(Params<R> p, int side
             o.n = 0;
             bool stepped = false;
             long long rsrc = 0;
+            long long r = 0;
             if (mine) {
-                const long long r = r0 + perm[pos];
+                r = r0 + perm[pos];
                 const uint32_t tv = iq.tv[r];
                 t.x[0] = iq.x[r];
                 t.x[1] = iq.y[r];
@@ -434,9 +449,13 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_interact(Params<R> p, int side
                     }
                     got = __shfl_sync(0xFFFFFFFFu, got, leader);
                     if (need && __popc(m & lanes_below) >= got) {
-                        // no room for the second output: discard the whole step
-                        load_track(qi, rsrc, t);
-                        copy_out(t, o);
+                        // no room for the second output: discard the step
+                        if constexpr (kPipe) {
+                            o.n = 0;
+                        } else {
+                            load_track(qi, rsrc, t);
+                            copy_out(t, o);
+                        }
                         stepped = false;
                     }
                 }
@@ -444,18 +463,129 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_interact(Params<R> p, int side
             if (stepped) apply_effects(p, t.ev, t.type, t.step, fx);
             {
                 const unsigned md = __ballot_sync(0xFFFFFFFFu, mine && !stepped);
-                if (lane == 0 && md) {
-                    atomicAdd(&p.total_steps[0], -(unsigned long long)__popc(md));
-                    atomicAdd(&p.total_steps[1], (unsigned long long)__popc(md));
+                if constexpr (kPipe) {
+                    // the step of an interacting track counts when it commits
+                    const unsigned mc = __ballot_sync(0xFFFFFFFFu, mine && stepped);
+                    if (lane == 0 && mc) atomicAdd(&p.total_steps[0], (unsigned long long)__popc(mc));
+                    if (lane == 0 && md) atomicAdd(&p.total_steps[1], (unsigned long long)__popc(md));
+                    if (md) {
+                        int base = 0;
+                        if (lane == 0) base = atomicAdd(n_next, __popc(md));
+                        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+                        if (mine && !stepped) {
+                            const long long k = (long long)base + __popc(md & lanes_below);
+                            if (k < p.Q)
+                                copy_record(iq, r, qnext, k);
+                            else
+                                atomicOr(p.status, kStatusQueueOverflow);
+                        }
+                    }
+                } else {
+                    if (lane == 0 && md) {
+                        atomicAdd(&p.total_steps[0], -(unsigned long long)__popc(md));
+                        atomicAdd(&p.total_steps[1], (unsigned long long)__popc(md));
+                    }
                 }
             }
-            emit<2>(p, qo, co, lane, o, t.x, t.ev, t.vol, select ? s_eh : nullptr);
+            emit<2>(p, qo, co, lane, o, t.x, t.ev, t.vol, eh);
         }
         __syncthreads();
     }
+}
+
+template <typename R, int BS, bool S, bool X>
+__global__ void __launch_bounds__(BS, 512 / BS) k_interact(Params<R> p, int side, int cin, int cout)
+{
+    constexpr int CH = BS * kInteractRecords;
+    __shared__ int s_chunk;
+    __shared__ int count[kNumModels];
+    __shared__ int offset[kNumModels + 1];
+    __shared__ unsigned short perm[CH];
+    __shared__ unsigned s_eh[S ? kEBins : 1];
+    constexpr bool select = S;
+    if constexpr (select) {
+        for (int b = threadIdx.x; b < kEBins; b += BS) s_eh[b] = 0u;
+        __syncthreads();
+    }
+    const long long ntot = (long long)p.cnt[cin].n[0] + p.cnt[cin].n[1];
+    interact_chunks<R, BS, X, false>(p, p.q[side], p.q[side ^ 1], &p.cnt[cout], cin, p.iq, p.cnt[cin].n_int,
+                                     p.Q - ntot, 2 * ntot <= p.Q, p.iq, nullptr, select ? s_eh : nullptr, s_chunk,
+                                     count, offset, perm);
     if constexpr (select) {
         for (int b = threadIdx.x; b < kEBins; b += BS)
             if (s_eh[b]) atomicAdd(&p.ehist[(size_t)cout * kEBins + b], s_eh[b]);
+    }
+}
+
+// Resident threads per SM of the pipelined kernel (its register budget).
+// FP64: 512 (128 registers, the interaction phase without spills); mixed
+// precision: 768 (about 80 registers, little spilled), whose extra
+// resident warps hide more of the transport phase's latency (+3% on the
+// calorimeter against 512; the FP64 kernel at 768 spills ~500 bytes a
+// thread and gains nothing).
+template <typename R>
+constexpr int pipe_threads_per_sm()
+{
+    return sizeof(R) == 8 ? 512 : 768;
+}
+
+// Pipelined schedule: one kernel per step-loop iteration.  Its blocks
+// first sample the interactions queued by the previous iteration (queue
+// iq_side[side ^ 1], block-level chunks sorted by model), then transport
+// this iteration's tracks a warp-sized chunk at a time, queueing the
+// tracks that interact in iq_side[side] (counted in the output counter
+// slot, so the next iteration finds them).  Transport and interaction work
+// of the same launch overlap on the GPU instead of running as two launches
+// one after the other; an interacting track's step simply completes one
+// iteration later.  Each input track and each queued record owns one output
+// slot; a record with two outputs takes a growth token from the rest.
+template <typename R, int BS, int G, bool X>
+__global__ void __launch_bounds__(BS, pipe_threads_per_sm<R>() / BS)
+    k_pipe(Params<R> p, int side, int cin, int cout, int cclr)
+{
+    constexpr int CH = BS * kInteractRecords;
+    __shared__ int s_chunk;
+    __shared__ int count[kNumModels];
+    __shared__ int offset[kNumModels + 1];
+    __shared__ unsigned short perm[CH];
+    if (blockIdx.x == 0 && threadIdx.x == 0) p.cnt[cclr] = Counters{};
+    const Tracks<R> qi = p.q[side];
+    const Tracks<R> qo = p.q[side ^ 1];
+    const InterQueue<R> q_prev = side ? p.iq : p.iq_alt;
+    const InterQueue<R> q_next = side ? p.iq_alt : p.iq;
+    int* const n_next = &p.cnt[cout].n_int;
+    const int nG = p.cnt[cin].n[0];
+    const int nC = p.cnt[cin].n[1];
+    const int n_prev = p.cnt[cin].n_int;
+    const long long Q = p.Q;
+    const long long ntot = (long long)nG + nC + n_prev;
+    Counters* const co = &p.cnt[cout];
+
+    // interactions of the previous iteration
+    interact_chunks<R, BS, X, true>(p, qi, qo, co, cin, q_prev, n_prev, Q - ntot, 2 * ntot <= Q, q_next, n_next,
+                                    nullptr, s_chunk, count, offset, perm);
+
+    // transport of this iteration's tracks (charged first in a field, in
+    // the order of k_sort_order)
+    const int lane = threadIdx.x & 31;
+    const int chunksG = (nG + 31) >> 5;
+    const int chunksC = (nC + 31) >> 5;
+    const bool charged_first = p.has_field != 0;
+    for (;;) {
+        int chunk = 0;
+        if (lane == 0) chunk = atomicAdd(&p.cnt[cin].work, 1);
+        chunk = __shfl_sync(0xFFFFFFFFu, chunk, 0);
+        if (chunk >= chunksG + chunksC) break;
+        const bool photon_chunk = charged_first ? chunk >= chunksC : chunk < chunksG;
+        const int local = photon_chunk ? (charged_first ? chunk - chunksC : chunk)
+                                       : (charged_first ? chunk : chunk - chunksG);
+        long long i = (long long)local * 32 + lane;
+        const bool active = i < (photon_chunk ? nG : nC);
+        if (charged_first && !photon_chunk && active) i = p.sperm[i];
+        const long long src = photon_chunk ? i : Q - nC + i;
+        TrackReg<R> t;
+        if (active) load_track(qi, src, t);
+        transport_lane<G, X>(p, qo, co, q_next, n_next, false, lane, t, active, false, src, nullptr);
     }
 }
 

@@ -17,7 +17,7 @@ from . import build as _build
 HOST, DEVICE = 0, 1
 PRECISION = {"fp64": 0, "mixed": 1}
 LOOP = {"plain": 0, "graph": 1, "persistent": 2}
-SCHEDULE = {"fused": 0, "split": 1}
+SCHEDULE = {"fused": 0, "split": 1, "pipelined": 2}
 SELECT = {"order": 0, "low_energy": 1}
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "CAPACITY", -3: "CUDA", -4: "BAD_STATE", -5: "TIMEOUT",
           -6: "NOT_READY", -7: "HOST_OOM"}
