@@ -58,7 +58,7 @@ TRAFFIC = {
 # in flops with add, sub, mul, div and sqrt one each and an fma two
 # (comparisons and elementary functions are listed there, not counted).  It
 # does not change when the kernels are optimised.
-FLOPS_PER_TRACK_STEP = {"calo": 43.09, "calo_field": 967.93, "cms": 73.49}
+FLOPS_PER_TRACK_STEP = {"calo": 43.09, "calo_field": 967.93, "cms": 73.49, "slab": 59.05, "batched": 969.84}
 # nominal FP64 peak of GB300: 152 SMs x 2 DFMA per clock x 2 flops x 2.06 GHz
 FP64_NOMINAL_GFLOPS = 1252.5
 KERNEL_SOURCES = ["emt_device.cuh", "emt_step.cuh", "emt_split.cuh", "emt_launch.cuh", "emt_kernels_fp64.cu",
@@ -373,7 +373,8 @@ def gpu_arm(args):
     peak = float(peaks.get("hbm_gbs", 6800.0))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": None, "peak_source": f"{src} hbm_gbs",
-            "kernel": ("step = k_transport + k_interact" if cfg.get("schedule") == "split" else "k_step"),
+            "kernel": {"split": "step = k_transport + k_interact",
+                       "pipelined": "step = k_pipe"}.get(cfg.get("schedule"), "k_step"),
             "launches": kern_launch, "mean_launch_ms": kern_ms / max(kern_launch, 1),
             "algorithmic_bytes_per_launch": state_bytes / max(kern_launch, 1),
             "kernel_share_of_step": kern_ms / total_ms}
@@ -568,13 +569,13 @@ def main():
                     help="served: step-loop drivers to compare (graph, persistent, plain)")
     ap.add_argument("--events", type=int, default=None, help="default 10,000 (100 for cms, cms_field)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--loop", default="auto", choices=["auto", "plain", "graph"],
+    ap.add_argument("--loop", default="auto", choices=["auto", "plain", "graph", "persistent"],
                     help="auto: autotune block size and loop driver on the workload first")
     ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")
     ap.add_argument("--graph-steps", type=int, default=12)
     ap.add_argument("--slots", type=int, default=1 << 25)
     ap.add_argument("--block", type=int, default=0)
-    ap.add_argument("--schedule", default="split", choices=["fused", "split"],
+    ap.add_argument("--schedule", default="split", choices=["fused", "split", "pipelined"],
                     help="step schedule when --loop is not auto")
     ap.add_argument("--one-at-a-time", type=int, default=100,
                     help="events of the plain one-event-at-a-time form to time (0: skip)")

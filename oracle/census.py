@@ -8,7 +8,7 @@ algorithmic FP64 work of the method, fixed by its definition and
 independent of any GPU code; the step kernels' arithmetic roofline is
 measured against them.
 
-    python oracle/census.py [workload ...]     (calo, calo_field, cms)
+    python oracle/census.py [workload ...]     (calo, calo_field, cms, slab, batched)
 
 prints one JSON line per workload: operations of each kind per track-step,
 flops per track-step (add, sub, mul, div and sqrt one each, fma two) and the
@@ -84,6 +84,15 @@ def main():
         elif name == "calo_field":
             s, n = W.calo_field_setup(), 100
             prim = W.calo_field_primaries(n)
+        elif name == "slab":
+            s, n = W.slab_setup(), 1000
+            prim = W.slab_primaries(n)
+        elif name == "batched":
+            # the first 6 of the 256 uneven events (1-64 primaries,
+            # 0.1-100 GeV) of the batched calorimeter-in-2-T workload
+            s, n = W.calo_field_setup(), 6
+            s.seed = 4
+            prim = W.subset(W.batched_primaries(256, seed=4), np.arange(n))
         else:
             s, n = W.cms_setup(), 4
             prim = W.cms_primaries(n, 1000)
