@@ -43,14 +43,16 @@ from paper_2203_09467_gb300 import workloads as W  # noqa: E402
 METRIC = "track-steps/s"
 
 # DRAM traffic per track-step of the step kernels (dram__bytes_read.sum +
-# dram__bytes_write.sum from ncu captures of a few launches of each step
-# kernel on a smaller run of the same workload, scaled by the launches'
-# track counts; summary and commands in profiles/).  Reported only while
-# the kernel sources are the ones that were measured (SHA-256 below).
+# dram__bytes_write.sum from ncu captures of four launches of one step
+# kernel on a smaller run of the same workload, divided by the tracks those
+# launches stepped; summary and commands in profiles/), per workload,
+# precision and step schedule.  Reported only while the kernel sources are
+# the ones that were measured (SHA-256 below).
 TRAFFIC = {
-    "kernel_sha256": "",
-    "bytes_per_track_step": {},
-    "source": "profiles/step_kernels_calo_dram_traffic.md",
+    "kernel_sha256": "edddce66b44705bf21794917aa5d2dd1c865e87fa11f5f0fedb60e477f7ab583",
+    "bytes_per_track_step": {"calo/fp64/pipelined": 105.7, "calo/mixed/pipelined": 96.4,
+                             "calo_field/fp64/split": 110.5},
+    "source": "profiles/step_kernels_dram_traffic.md",
 }
 # Algorithmic FP64 work of one track-step of the method, fixed by its
 # definition: a census of the FP64 operations of the oracle's step on the
@@ -378,7 +380,7 @@ def gpu_arm(args):
             "launches": kern_launch, "mean_launch_ms": kern_ms / max(kern_launch, 1),
             "algorithmic_bytes_per_launch": state_bytes / max(kern_launch, 1),
             "kernel_share_of_step": kern_ms / total_ms}
-    key = f"{args.workload}/{args.precision}"
+    key = f"{args.workload}/{args.precision}/{cfg.get('schedule', 'fused')}"
     current = TRAFFIC["kernel_sha256"] == kernel_sha256()
     per_step = TRAFFIC["bytes_per_track_step"].get(key) if current else None
     steps_per_launch = steps_done / max(kern_launch, 1)
@@ -458,11 +460,16 @@ def gpu_arm(args):
         "config": {"workload": desc, "precision": args.precision, "schedule": cfg.get("schedule", "fused"),
                    "loop": cfg["loop_mode"],
                    "graph_steps": cfg["graph_steps"], "block": cfg["block_size"] or 256,
+                   "track_selection": {k: cfg[k] for k in ("max_active", "select", "spill_above") if k in cfg} or None,
                    "slot_capacity": args.slots, "events_per_gpu": n, "events_total": n_total,
                    "partition": "one workload split across the GPUs by cost (greedy on primary energy)",
                    "l2": "512 MB buffer written between timed steps; track state >> L2"},
         "events_per_s": n * world / (total_ms_all / 1e3 / args.steps),
         "iterations_per_step": stats[0]["iterations"], "peak_tracks": max(s["peak_tracks"] for s in stats),
+        # per timed step: steps deferred for want of a slot, tracks moved to
+        # host memory and back, tracks held by the selection, RK4 substeps
+        "run_stats_per_step": {k: sum(s[k] for s in stats) / len(stats)
+                               for k in ("deferred", "spilled", "held", "rk4_substeps")},
         "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": launches,
         "gather": gather,

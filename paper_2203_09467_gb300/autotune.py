@@ -9,9 +9,14 @@ or 256 threads: a larger block regroups more interacting tracks per model, a
 smaller one leaves more blocks per SM) and the step-loop driver (a host loop
 with one counter read per step, CUDA graphs of 12 or 24 steps with one
 counter read per graph, or the persistent kernel that runs up to 64 or 256
-fused steps per launch with a grid barrier between steps).  Every candidate
-transports the same batch of events; the fastest by CUDA-event time wins.  Results are cached per GPU name, workload
-name and precision in a JSON file next to this module.
+fused steps per launch with a grid barrier between steps).  Two more
+candidates select the lowest-energy tracks (split schedule, at most 3/4 or
+5/8 of the track store stepped per iteration): where the showers outgrow
+the store, holding the most energetic tracks back lets the others finish
+instead of deferring steps for want of a slot.  Every candidate
+transports the same batch of events; the fastest by CUDA-event time wins.
+Results are cached per GPU name, workload name, precision and track-store
+size in a JSON file next to this module.
 """
 from __future__ import annotations
 
@@ -36,9 +41,21 @@ CANDIDATES = [
 ]
 
 
-def _key(name, precision):
+def selection_candidates(slot_capacity):
+    """Low-energy track selection with budgets of 3/4 and 5/8 of the store
+    (the second moves held tracks to host memory above 13/16)."""
+    q = int(slot_capacity)
+    return [
+        {"block_size": 256, "loop_mode": "graph", "graph_steps": 24, "schedule": "split",
+         "max_active": 3 * q // 4, "select": "low_energy"},
+        {"block_size": 256, "loop_mode": "graph", "graph_steps": 24, "schedule": "split",
+         "max_active": 5 * q // 8, "select": "low_energy", "spill_above": 13 * q // 16},
+    ]
+
+
+def _key(name, precision, slot_capacity):
     import torch
-    return f"{torch.cuda.get_device_name()}|{name}|{precision}"
+    return f"{torch.cuda.get_device_name()}|{name}|{precision}|{int(slot_capacity)}"
 
 
 def time_config(setup, prim, ids, precision, cfg, repeats=2, slot_capacity=1 << 25, device=0):
@@ -68,7 +85,7 @@ def time_config(setup, prim, ids, precision, cfg, repeats=2, slot_capacity=1 << 
 def autotune(name, setup, prim, ids, precision="fp64", use_cache=True, repeats=2, slot_capacity=1 << 25,
              device=0, candidates=None):
     """Return (best configuration, {candidate: ms}) for this workload."""
-    key = _key(name, precision)
+    key = _key(name, precision, slot_capacity)
     cache = {}
     if use_cache and os.path.exists(CACHE):
         try:
@@ -79,7 +96,7 @@ def autotune(name, setup, prim, ids, precision="fp64", use_cache=True, repeats=2
         return cache[key]["best"], cache[key]["timings"]
     timings = {}
     best, best_ms = None, float("inf")
-    for cfg in candidates or CANDIDATES:
+    for cfg in candidates or (CANDIDATES + selection_candidates(slot_capacity)):
         ms = time_config(setup, prim, ids, precision, cfg, repeats, slot_capacity, device)
         timings[json.dumps(cfg, sort_keys=True)] = ms
         if ms < best_ms:

@@ -28,13 +28,16 @@ __device__ __forceinline__ uint32_t pack_tvm(int type, int vol, int model)
 // policy; both kernels count their outputs' energy classes for the next
 // step's selection.
 // Resident threads per SM the transport kernel is compiled for (its
-// register budget): measured on GB300, the FP64 kernel runs fastest with 768
-// (80 registers, a few hundred bytes of spills, 50% more warps to hide the
-// FP64 pipe's latency than with 512), the mixed kernel with 640.
+// register budget), measured on GB300.  FP64: 512 (128 registers, almost no
+// spills).  In a field the RK4 substeps keep many doubles live; at 768
+// threads (80 registers) their spills share the FP64 unit's issue queue,
+// and the field transport runs 13% slower.  Without a field 768 was 1% faster,
+// but there the pipelined schedule is used.  Mixed precision: 640 (768
+// measured 14% slower in the field, 2% faster on the cylinder problem).
 template <typename R>
 constexpr int transport_threads_per_sm()
 {
-    return sizeof(R) == 8 ? 768 : 640;
+    return sizeof(R) == 8 ? 512 : 640;
 }
 
 // Phase A of one track in the transport kernel (every lane of the warp
