@@ -124,6 +124,24 @@ def test_cms_event_parity(emt, oracle_mod, schedule):
     assert st["track_steps"] == int(osumm[:, 4].sum())
 
 
+def test_cms_full_size(emt, oracle_mod):
+    """Sec. 3.2's problem at its full size (100 events x 1000 isotropic
+    photons of 1 GeV, 8.0e7 track-steps), in the benchmark's launch
+    configuration (split schedule, graphs of 12 steps, 2^25 slots): every
+    event, its z profile and the steps-per-track histogram match the
+    oracle (about 1 s on 16 cores)."""
+    s = W.cms_setup()
+    n = 100
+    prim = W.cms_primaries(n, 1000)
+    nb = 4096
+    hist, summ, st, sh = gpu_run(emt, s, prim, n, schedule="split", loop_mode="graph", graph_steps=12,
+                                 slot_capacity=1 << 25, step_hist_bins=nb)
+    ohist, osumm, osh = oracle_of(oracle_mod, s).run(prim, n, np.arange(n), step_bins=nb)
+    check_events(summ, osumm, hist, ohist)
+    assert np.array_equal(sh, osh)
+    assert st["track_steps"] == int(osumm[:, 4].sum())
+
+
 def test_cms_field_parity(emt, oracle_mod):
     s = W.cms_field_setup()
     n = 8

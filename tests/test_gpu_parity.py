@@ -174,30 +174,55 @@ def test_event_parity_calo(emt, oracle_mod):
 
 def test_event_parity_field_fp64(emt, oracle_mod):
     """The calorimeter in 2 T with its stated primaries (e-, e+, gamma of
-    1-100 GeV within 10 degrees), 1,000 events in FP64: totals and every
+    1-100 GeV within 10 degrees), all 10,000 events in FP64, in the
+    benchmark's launch configuration for this workload (split schedule with
+    the cost sort, CUDA graphs of 24 steps, 2^25 slots): totals and every
     layer to 1e-9 of the event energy and identical step and track counts
-    on >= 99.9% of events (measured on GB300: every event, worst 5e-14,
-    also over all 10,000 events of the workload), and the longitudinal
-    profile at p > 0.01."""
+    on >= 99.9% of events (measured on GB300: every event, worst 5e-14), and
+    the longitudinal profile at p > 0.01.  The oracle takes about 17 s on 16
+    cores."""
     from stats_util import profile_test
     s = W.calo_field_setup()
-    n = 1000
+    n = 10000
     prim = W.calo_field_primaries(n)
-    hist, summ, st = gpu_run(emt, s, prim, n, slot_capacity=1 << 24)
+    hist, summ, st = gpu_run(emt, s, prim, n, slot_capacity=1 << 25, schedule="split", loop_mode="graph",
+                             graph_steps=24)
     ohist, osumm = oracle_of(oracle_mod, s).run(prim, n, np.arange(n))
     compare_events(summ, osumm, hist, ohist)
     assert profile_test(hist, ohist)[2] > 0.01
+    assert st["rk4_substeps"] > 5 * st["track_steps"]
+
+
+def test_full_size_batched_fp64(emt, oracle_mod):
+    """The batched workload at its stated size: 256 events of 1-64 e-, e+
+    and gamma primaries of 0.1-100 GeV in the 2 T calorimeter, on a 2^20-slot
+    track store, in the autotuner's choice for it (pipelined schedule,
+    graphs of 24 steps).  The showers outgrow the store, so hundreds of
+    millions of interactions wait in the queue for a slot; every result must
+    still match the oracle per event."""
+    from stats_util import profile_test
+    s = W.calo_field_setup()
+    s.seed = 4
+    n = 256
+    prim = W.batched_primaries(n, seed=4)
+    hist, summ, st = gpu_run(emt, s, prim, n, slot_capacity=1 << 20, schedule="pipelined", loop_mode="graph",
+                             graph_steps=24, block_size=128)
+    assert st["deferred"] > 0 and st["peak_tracks"] <= 1 << 20
+    ohist, osumm = oracle_of(oracle_mod, s).run(prim, n, np.arange(n))
+    compare_events(summ, osumm, hist, ohist)
+    assert profile_test(hist, ohist)[2] > 0.01
+    assert st["track_steps"] == int(osumm[:, 4].sum())
 
 
 def test_full_size_calo(emt, oracle_mod):
     """The 10,000-event 10 GeV calorimeter, every event recomputed by the
     oracle (about 2 s on 16 cores), in the benchmark's launch configuration
-    (split schedule, CUDA graphs of 24 steps, 2^25 slots)."""
+    (pipelined schedule, 256 threads, CUDA graphs of 24 steps, 2^25 slots)."""
     s = W.calo_setup()
     n = 10000
     prim = W.calo_primaries(n)
-    hist, summ, st = gpu_run(emt, s, prim, n, slot_capacity=1 << 25, max_events=n, schedule="split",
-                             loop_mode="graph", graph_steps=24)
+    hist, summ, st = gpu_run(emt, s, prim, n, slot_capacity=1 << 25, max_events=n, schedule="pipelined",
+                             loop_mode="graph", graph_steps=24, block_size=256)
     ohist, osumm = oracle_of(oracle_mod, s).run(prim, n, np.arange(n))
     compare_events(summ, osumm, hist, ohist)
     assert st["track_steps"] == int(osumm[:, 4].sum())
