@@ -222,6 +222,10 @@ void set_geometry(Params<R>& p, int n, const emt_world* w)
     p.n_layers = n;
     p.hx = w->half_x_cm;
     p.hy = w->half_y_cm;
+    p.kxy[0] = ord_key(-p.hx + kChordMargin);
+    p.kxy[1] = ord_key(p.hx - kChordMargin);
+    p.kxy[2] = ord_key(-p.hy + kChordMargin);
+    p.kxy[3] = ord_key(p.hy - kChordMargin);
     for (int a = 0; a < 3; ++a) {
         p.wlo[a] = w->lo_cm[a];
         p.whi[a] = w->hi_cm[a];

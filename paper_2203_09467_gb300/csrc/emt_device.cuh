@@ -13,6 +13,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <math.h>
+#include <string.h>
 
 namespace emt {
 
@@ -196,6 +197,10 @@ struct Params {
     const int* lbin;
     int n_layers;
     double hx, hy;
+    // ord_key of the lateral bounds of a layer's chord test, formed once
+    // when the geometry is loaded: -hx + m, hx - m, -hy + m, hy - m
+    // (m = kChordMargin)
+    long long kxy[4];
     double wlo[3], whi[3];
     double B[3];
     double bmag;
@@ -405,6 +410,21 @@ __device__ __forceinline__ bool lt_pos(float a, float b) { return a < b; }
 __device__ __forceinline__ bool gt_zero(double a) { return __double_as_longlong(a) > 0; }
 __device__ __forceinline__ bool gt_zero(float a) { return a > 0.0f; }
 __device__ __forceinline__ bool nonzero(double a) { return ((unsigned long long)__double_as_longlong(a) << 1) != 0ull; }
+// An integer key whose signed order is the numeric order of any two
+// non-NaN doubles of either sign: the magnitude bits, negated for a
+// negative value (so -0 and +0 both map to 0).  A NaN maps beyond every
+// finite value on its sign's side.
+__host__ __device__ __forceinline__ long long ord_key(double a)
+{
+#ifdef __CUDA_ARCH__
+    const long long b = __double_as_longlong(a);
+#else
+    long long b;
+    memcpy(&b, &a, sizeof b);
+#endif
+    const long long m = b & 0x7fffffffffffffffll;
+    return b < 0 ? -m : m;
+}
 
 // node n with grid[n] <= E < grid[n+1], clamped to [0, n_grid-2]: an FP32
 // logarithm guesses, exact comparisons with the nodes decide.
@@ -747,9 +767,11 @@ __device__ __forceinline__ Exit nav_exit(const Params<R>& p, int vol, const doub
 // its derivatives are evaluated in R (FP64 path: double, in the operation
 // order of the definition; mixed path: float), positions accumulate in FP64.
 template <typename R>
-__device__ __forceinline__ void rk4(const Params<R>& p, R kq, const double x[3], const R u[3], R hs, double xo[3],
-                                    R uo[3])
+__device__ __forceinline__ void rk4(const Params<R>& p, R kq, const double x[3], const R u[3], R hs, R h6,
+                                    double xo[3], R uo[3])
 {
+    // h6 = hs / 6, rounded once by the caller (the same quotient for every
+    // substep of one length)
     // products added to a sum are fused (one rounding each), as in the oracle
     const R B0 = from_d<R>(p.B[0]), B1 = from_d<R>(p.B[1]), B2 = from_d<R>(p.B[2]);
     R a1[3], a2[3], a3[3], a4[3], u2[3], u3[3], u4[3];
@@ -772,7 +794,6 @@ __device__ __forceinline__ void rk4(const Params<R>& p, R kq, const double x[3],
     a4[0] = kq * mfma(u4[1], B2, -(u4[2] * B1));
     a4[1] = kq * mfma(u4[2], B0, -(u4[0] * B2));
     a4[2] = kq * mfma(u4[0], B1, -(u4[1] * B0));
-    R h6 = hs / R(6);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const R su = mfma(R(2), u3[i], mfma(R(2), u2[i], u[i])) + u4[i];
@@ -849,6 +870,30 @@ __device__ __forceinline__ bool chord_inside(const Params<R>& p, int vol, const 
     return false;
 }
 
+// The chord test of a layer (vol >= 0, layered geometry) as integer
+// comparisons through ord_key, whose order is the numeric order of non-NaN
+// values: the lateral bounds' keys are formed when the geometry is loaded
+// (Params::kxy), the layer's two z bounds per substep (held across the
+// substep loop they cost registers, and spills, in the mixed-precision
+// kernel), each with the same sum chord_inside forms.  A NaN coordinate fails one of the two tests
+// of its axis in both forms, so every decision equals chord_inside's.
+struct LayerBox {
+    long long zlo, zhi;
+};
+
+template <typename R>
+__device__ __forceinline__ LayerBox layer_box(const Params<R>& p, int vol)
+{
+    return LayerBox{ord_key(p.zb[vol] + kChordMargin), ord_key(p.zb[vol + 1] - kChordMargin)};
+}
+
+template <typename R>
+__device__ __forceinline__ bool inside_box(const Params<R>& p, const LayerBox& b, const double x1[3])
+{
+    const long long k0 = ord_key(x1[0]), k1 = ord_key(x1[1]), k2 = ord_key(x1[2]);
+    return k2 > b.zlo && k2 < b.zhi && k0 > p.kxy[0] && k0 < p.kxy[1] && k1 > p.kxy[2] && k1 < p.kxy[3];
+}
+
 // n substeps of length hs (the caller derives both from h_max); the chord
 // of each substep is tested against the current volume and a crossing at
 // fraction f repeats the substep with h f, snapped onto the plane.
@@ -860,18 +905,22 @@ __device__ __forceinline__ double propagate_field(const Params<R>& p, int charge
     double kq = charge * kFieldC / pm;
     double s = 0.0;
     *crossed = false;
+    const R hsr = R(hs);
+    const R h6 = hsr / R(6);
+    const bool boxed = G == kGeomLayers && vol >= 0;
     for (int i = 0; i < n; ++i) {
         double x1[3], c[3];
         R u1[3];
-        rk4(p, R(kq), x, u, R(hs), x1, u1);
+        rk4(p, R(kq), x, u, hsr, h6, x1, u1);
         *evals += 1;
-        if (!chord_inside<G>(p, vol, x, x1)) {
+        if (!(boxed ? inside_box(p, layer_box(p, vol), x1) : chord_inside<G>(p, vol, x, x1))) {
 #pragma unroll
             for (int a = 0; a < 3; ++a) c[a] = x1[a] - x[a];
             Exit e = nav_exit<G>(p, vol, x, c);
             if (e.t <= 1.0) {
                 double h2 = hs * e.t;
-                rk4(p, R(kq), x, u, R(h2), x1, u1);
+                const R h2r = R(h2);
+                rk4(p, R(kq), x, u, h2r, h2r / R(6), x1, u1);
                 *evals += 1;
                 if (e.axis >= 0) x1[e.axis] = e.plane;
 #pragma unroll
