@@ -121,10 +121,23 @@ struct Tracks {
     uint32_t* tv;    // type (bits 0-7) | (volume + 2) << 8
 };
 
-// scheduling classes of charged tracks in a field (split schedule): class
-// c holds the tracks whose estimated RK4 substep count n satisfies
-// (kMaxSubsteps - n) >> 2 == c, so class 0 is the most expensive
+// scheduling classes of charged tracks in a field: class 0 holds the most
+// expensive tracks (an estimated 72 or more RK4 substeps), classes 1-7 hold
+// ranges of 2 to 16 substep counts, and classes 8-27 hold a single count
+// each, 20 down to 1, where most tracks of a calorimeter lie
 constexpr int kSortKeys = 32;
+__host__ __device__ constexpr int substep_class(int n)
+{
+    return n <= 20   ? 28 - n
+           : n <= 22 ? 7
+           : n <= 25 ? 6
+           : n <= 29 ? 5
+           : n <= 35 ? 4
+           : n <= 43 ? 3
+           : n <= 55 ? 2
+           : n <= 71 ? 1
+                     : 0;
+}
 
 // state of the grid barrier of the persistent step loop (zeroed before
 // each launch)

@@ -132,7 +132,9 @@ __global__ void __launch_bounds__(256) k_sort_keys(Params<R> p, int side, int ci
         const uint32_t tv = qi.tv[base + i];
         t.type = tv_type(tv);
         t.vol = tv_vol(tv);
-        const int cls = (kMaxSubsteps - field_substeps_estimate(p, t)) >> 2;
+        t.x[2] = qi.z[base + i];
+        t.u[2] = qi.uz[base + i];
+        const int cls = substep_class(field_substeps_estimate(p, t));
         p.skey[i] = (uint8_t)cls;
         atomicAdd(&h[cls], 1);
     }

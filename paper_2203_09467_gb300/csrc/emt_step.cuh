@@ -459,10 +459,11 @@ __device__ __forceinline__ void interaction_part(const Params<R>& p, TrackReg<R>
 
 // Scheduling key of a charged track's next step in a field: an estimate,
 // in FP32, of its number of RK4 substeps, ceil(s / h_max) with s the
-// smallest of the free path (draw 0 of the step), the range limit and the
-// field-step limits, clamped to [1, kMaxSubsteps].  Boundaries are ignored
-// (an upper bound).  It only decides which lanes run together; the step
-// itself recomputes everything in the method's own arithmetic.
+// smallest of the free path (draw 0 of the step), the range limit, the
+// field-step limits and, in a layer, the straight-line distance to the
+// z plane ahead (curvature ignored), clamped to [1, kMaxSubsteps].  It only
+// decides which lanes run together; the step itself recomputes everything
+// in the method's own arithmetic.
 template <typename R>
 __device__ __forceinline__ int field_substeps_estimate(const Params<R>& p, const TrackReg<R>& t)
 {
@@ -488,6 +489,16 @@ __device__ __forceinline__ int field_substeps_estimate(const Params<R>& p, const
             const float u = __uint_as_float(0x3F800000u | (dr.w[1] >> 9)) - (1.0f - 0x1p-24f);
             s = fminf(s, -__logf(u) / sig);
         }
+    }
+    if (p.geom == kGeomLayers && t.vol >= 0) {
+        // the straight-line distance to the layer's z plane ahead: the step
+        // ends there after about that many substeps and one repeated one
+        const float uz = est_f(t.u[2]);
+        const float z = (float)t.x[2];
+        float dz = 3.0e38f;
+        if (uz > 0.0f) dz = ((float)p.zb[t.vol + 1] - z) / uz;
+        if (uz < 0.0f) dz = (z - (float)p.zb[t.vol]) / -uz;
+        s = fminf(s, fmaxf(dz, 0.0f) + hmax);
     }
     const float n = ceilf(s / hmax);
     return n < 1.0f ? 1 : (n > (float)kMaxSubsteps ? kMaxSubsteps : (int)n);
