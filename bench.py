@@ -49,9 +49,9 @@ METRIC = "track-steps/s"
 # precision and step schedule.  Reported only while the kernel sources are
 # the ones that were measured (SHA-256 below).
 TRAFFIC = {
-    "kernel_sha256": "edddce66b44705bf21794917aa5d2dd1c865e87fa11f5f0fedb60e477f7ab583",
-    "bytes_per_track_step": {"calo/fp64/pipelined": 105.7, "calo/mixed/pipelined": 96.4,
-                             "calo_field/fp64/split": 110.5},
+    "kernel_sha256": "b76c91082e324a61b9c70d4553cf02db214d4c755e89f38ff1a800db5911f955",
+    "bytes_per_track_step": {"calo/fp64/pipelined": 101.6, "calo/fp64/split": 114.4, "calo/mixed/pipelined": 97.5,
+                             "calo_field/fp64/split": 109.1},
     "source": "profiles/step_kernels_dram_traffic.md",
 }
 # Algorithmic FP64 work of one track-step of the method, fixed by its
@@ -63,8 +63,10 @@ TRAFFIC = {
 FLOPS_PER_TRACK_STEP = {"calo": 43.09, "calo_field": 967.93, "cms": 73.49, "slab": 59.05, "batched": 969.84}
 # nominal FP64 peak of GB300: 152 SMs x 2 DFMA per clock x 2 flops x 2.06 GHz
 FP64_NOMINAL_GFLOPS = 1252.5
-KERNEL_SOURCES = ["emt_device.cuh", "emt_step.cuh", "emt_split.cuh", "emt_launch.cuh", "emt_kernels_fp64.cu",
-                  "emt_kernels_mixed.cu"]
+KERNEL_SOURCES = ["emt_device.cuh", "emt_intdiv.cuh", "emt_intlog.cuh", "emt_logtab.h", "emt_step.cuh",
+                  "emt_split.cuh", "emt_launch.cuh", "emt_kernels_fp64.cu", "emt_kernels_fp64_persist.cu",
+                  "emt_kernels_fp64_split.cu", "emt_kernels_fp64_pipe.cu", "emt_kernels_mixed.cu",
+                  "emt_kernels_mixed_persist.cu", "emt_kernels_mixed_split.cu", "emt_kernels_mixed_pipe.cu"]
 
 
 def kernel_sha256() -> str:

@@ -23,7 +23,13 @@ UNITS = {
     "emt_api.cu": [],
     "emt_tables.cu": ["--fmad=false"],
     "emt_kernels_fp64.cu": ["--fmad=false"],
+    "emt_kernels_fp64_persist.cu": ["--fmad=false"],
+    "emt_kernels_fp64_split.cu": ["--fmad=false"],
+    "emt_kernels_fp64_pipe.cu": ["--fmad=false"],
     "emt_kernels_mixed.cu": [],
+    "emt_kernels_mixed_persist.cu": [],
+    "emt_kernels_mixed_split.cu": [],
+    "emt_kernels_mixed_pipe.cu": [],
     "emt_serve.cu": [],
     "emt_peak.cu": [],
 }

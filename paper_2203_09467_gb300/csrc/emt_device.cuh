@@ -15,6 +15,9 @@
 #include <math.h>
 #include <string.h>
 
+#include "emt_intdiv.cuh"
+#include "emt_intlog.cuh"
+
 namespace emt {
 
 constexpr double kMe = 0.51099895;          // electron mass, MeV (CODATA 2018)
@@ -52,7 +55,8 @@ constexpr int kStatusBadTrack = 2;
 constexpr int kStatusTimeout = 4;  // a bounded device wait gave up (persistent step loop)
 
 // ------------------------------------------------------------------ math
-__device__ __forceinline__ double mlog(double x) { return log(x); }
+// FP64 logarithm on the integer pipe (emt_intlog.cuh), FP32 native
+__device__ __forceinline__ double mlog(double x) { return intlog::log_rn(x); }
 __device__ __forceinline__ float mlog(float x) { return logf(x); }
 __device__ __forceinline__ double mexp(double x) { return exp(x); }
 __device__ __forceinline__ float mexp(float x) { return expf(x); }
@@ -64,13 +68,25 @@ __device__ __forceinline__ double mexpm1(double x) { return expm1(x); }
 __device__ __forceinline__ float mexpm1(float x) { return expm1f(x); }
 __device__ __forceinline__ double mlog1p(double x) { return log1p(x); }
 __device__ __forceinline__ float mlog1p(float x) { return log1pf(x); }
-__device__ __forceinline__ double msqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ double msqrt(double x) { return intdiv::sqrt_rn(x); }  // integer pipe, exact
 __device__ __forceinline__ float msqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double msin(double x) { return sin(x); }
 __device__ __forceinline__ float msin(float x) { return sinf(x); }
 __device__ __forceinline__ double mcos(double x) { return cos(x); }
 __device__ __forceinline__ float mcos(float x) { return cosf(x); }
 __device__ __forceinline__ double mfmax(double a, double b) { return fmax(a, b); }
+// a / b: FP64 quotients on the integer pipe (bit-identical to the IEEE
+// division; GB300's FP64 pipe is its narrowest), FP32 quotients native
+__device__ __forceinline__ double mdiv(double a, double b) { return intdiv::div_rn(a, b); }
+__device__ __forceinline__ float mdiv(float a, float b) { return a / b; }
+// a quotient whose divisor several numerators share
+struct DivisorF {
+    float y;
+};
+__device__ __forceinline__ intdiv::Divisor mdivisor(double y) { return intdiv::divisor(y); }
+__device__ __forceinline__ DivisorF mdivisor(float y) { return DivisorF{y}; }
+__device__ __forceinline__ double mdiv(double a, const intdiv::Divisor& d) { return intdiv::div_rn(a, d); }
+__device__ __forceinline__ float mdiv(float a, const DivisorF& d) { return a / d.y; }
 __device__ __forceinline__ float mfmax(float a, float b) { return fmaxf(a, b); }
 
 // ------------------------------------------------------------------ conversions
@@ -497,7 +513,7 @@ __device__ __forceinline__ R xs_value(const Params<R>& p, const R* t, const R* d
 template <typename R>
 __device__ __forceinline__ R range_value(const Params<R>& p, const R* t, const R* dt, R T, const Lookup<R>& l)
 {
-    if (lt_pos(T, p.grid[0])) return t[3] * (T / p.grid[0]);
+    if (lt_pos(T, p.grid[0])) return t[3] * mdiv(T, p.grid[0]);
     int n = l.n;
     R f = l.f;
     if (l.clamp > 0) f = (T - p.grid[n]) * p.igrid[n];
@@ -510,7 +526,7 @@ __device__ __forceinline__ R range_value(const Params<R>& p, const R* t, const R
 template <typename R>
 __device__ __forceinline__ R inv_range(const Params<R>& p, const R* t, const R* irs, R r, int nstart)
 {
-    if (lt_pos(r, t[3])) return p.grid[0] * (r / t[3]);
+    if (lt_pos(r, t[3])) return p.grid[0] * mdiv(r, t[3]);
     int n = nstart;
     while (n > 0 && !le_pos(t[n * kNq + 3], r)) --n;
     int top = p.n_grid - 2;
@@ -562,7 +578,7 @@ __device__ __forceinline__ Exit nav_exit_cyl(const Params<R>& p, int vol, const 
     e.plane = 0.0;
     if (d[2] != 0.0) {
         const double pl = d[2] > 0.0 ? p.half_z : -p.half_z;
-        e.t = (pl - x[2]) / d[2];
+        e.t = mdiv(pl - x[2], d[2]);
         e.axis = 2;
         e.plane = pl;
     }
@@ -574,8 +590,8 @@ __device__ __forceinline__ Exit nav_exit_cyl(const Params<R>& p, int vol, const 
         const double c = q - ro * ro;
         double disc = b * b - a * c;
         if (disc < 0.0) disc = 0.0;
-        const double sq = sqrt(disc);
-        const double t = b > 0.0 ? -c / (b + sq) : (sq - b) / a;
+        const double sq = msqrt(disc);
+        const double t = b > 0.0 ? mdiv(-c, b + sq) : mdiv(sq - b, a);
         if (t < e.t) {
             e.t = t;
             e.axis = -1;
@@ -587,7 +603,7 @@ __device__ __forceinline__ Exit nav_exit_cyl(const Params<R>& p, int vol, const 
             const double ci = q - ri * ri;
             const double di = b * b - a * ci;
             if (di >= 0.0) {
-                const double ti = ci / (sqrt(di) - b);
+                const double ti = mdiv(ci, msqrt(di) - b);
                 if (ti < e.t) {
                     e.t = ti;
                     e.axis = -1;
@@ -709,7 +725,7 @@ __device__ __forceinline__ Exit nav_exit_layers(const Params<R>& p, int vol, con
         for (int oi = 0; oi < 3; ++oi) {
             const int a = order[oi];
             if (!has[a] || (sure[a] && !(tf[a] <= thr))) continue;
-            double t = diff[a] / d[a];
+            double t = mdiv(diff[a], d[a]);
             if (t < e.t) {
                 e.t = t;
                 e.next = nx[a];
@@ -726,7 +742,7 @@ __device__ __forceinline__ Exit nav_exit_layers(const Params<R>& p, int vol, con
             int a = order[oi];
             if (d[a] == 0.0) continue;
             double pl = d[a] > 0.0 ? lo[a] : hi[a];
-            double t = (pl - x[a]) / d[a];
+            double t = mdiv(pl - x[a], d[a]);
             if (!(t >= 0.0) || !(t < e.t)) continue;
             bool ok = true;
             double qz = 0.0;
@@ -751,7 +767,7 @@ __device__ __forceinline__ Exit nav_exit_layers(const Params<R>& p, int vol, con
             int a = order[oi];
             if (d[a] == 0.0) continue;
             double pl = d[a] > 0.0 ? p.whi[a] : p.wlo[a];
-            double t = (pl - x[a]) / d[a];
+            double t = mdiv(pl - x[a], d[a]);
             if (t < e.t) {
                 e.t = t;
                 e.next = kVolOut;
@@ -817,9 +833,9 @@ __device__ __forceinline__ void rk4(const Params<R>& p, R kq, const double x[3],
             xo[i] = x[i] + to_d(h6 * su);
         uo[i] = mfma(h6, sa, u[i]);
     }
-    R n = msqrt(mfma(uo[0], uo[0], mfma(uo[1], uo[1], uo[2] * uo[2])));
+    const auto nd = mdivisor(msqrt(mfma(uo[0], uo[0], mfma(uo[1], uo[1], uo[2] * uo[2]))));
 #pragma unroll
-    for (int i = 0; i < 3; ++i) uo[i] = uo[i] / n;
+    for (int i = 0; i < 3; ++i) uo[i] = mdiv(uo[i], nd);
 }
 
 // True when the chord from x (inside volume vol) to x1 cannot leave vol:
@@ -861,7 +877,7 @@ __device__ __forceinline__ bool chord_inside(const Params<R>& p, int vol, const 
             if (!(q1 > ri2) || !(q0 > ri2)) return false;
             const double cx = x1[0] - x[0], cy = x1[1] - x[1];
             const double a = cx * cx + cy * cy, b = x[0] * cx + x[1] * cy;
-            if (b < 0.0 && -b < a && !(q0 - b * (b / a) > ri2)) return false;
+            if (b < 0.0 && -b < a && !(q0 - b * mdiv(b, a) > ri2)) return false;
         }
         return true;
     }
@@ -915,11 +931,11 @@ template <int G, typename R>
 __device__ __forceinline__ double propagate_field(const Params<R>& p, int charge, double pm, int vol, double x[3],
                                                   R u[3], int n, double hs, Exit* bnd, bool* crossed, int* evals)
 {
-    double kq = charge * kFieldC / pm;
+    double kq = mdiv(charge * kFieldC, pm);
     double s = 0.0;
     *crossed = false;
     const R hsr = R(hs);
-    const R h6 = hsr / R(6);
+    const R h6 = mdiv(hsr, R(6));
     const bool boxed = G == kGeomLayers && vol >= 0;
     for (int i = 0; i < n; ++i) {
         double x1[3], c[3];
@@ -933,7 +949,7 @@ __device__ __forceinline__ double propagate_field(const Params<R>& p, int charge
             if (e.t <= 1.0) {
                 double h2 = hs * e.t;
                 const R h2r = R(h2);
-                rk4(p, R(kq), x, u, h2r, h2r / R(6), x1, u1);
+                rk4(p, R(kq), x, u, h2r, mdiv(h2r, R(6)), x1, u1);
                 *evals += 1;
                 if (e.axis >= 0) x1[e.axis] = e.plane;
 #pragma unroll
@@ -969,8 +985,8 @@ __device__ __forceinline__ void rotate(const R u[3], R cost, R phi, R out[3])
     R perp2 = u[0] * u[0] + u[1] * u[1];
     if (perp2 > R(1e-20)) {
         R up = msqrt(perp2);
-        out[0] = (u[0] * u[2] * a - u[1] * b) / up + u[0] * cost;
-        out[1] = (u[1] * u[2] * a + u[0] * b) / up + u[1] * cost;
+        out[0] = mdiv(u[0] * u[2] * a - u[1] * b, up) + u[0] * cost;
+        out[1] = mdiv(u[1] * u[2] * a + u[0] * b, up) + u[1] * cost;
         out[2] = -up * a + u[2] * cost;
     } else if (u[2] >= R(0)) {
         out[0] = a;
@@ -992,9 +1008,10 @@ __device__ __forceinline__ bool momentum_balance(R pa, const R da[3], R pb, cons
     R v2 = pa * da[2] - pb * db[2];
     R n = msqrt(v0 * v0 + v1 * v1 + v2 * v2);
     if (!(n > R(0))) return false;
-    out[0] = v0 / n;
-    out[1] = v1 / n;
-    out[2] = v2 / n;
+    const auto nd = mdivisor(n);
+    out[0] = mdiv(v0, nd);
+    out[1] = mdiv(v1, nd);
+    out[2] = mdiv(v2, nd);
     return true;
 }
 
@@ -1018,24 +1035,24 @@ template <typename R>
 __device__ __forceinline__ void sample_compton(Draws& d, R k, R dir[3], Products<R>& out, R& knew)
 {
     const R me = R(kMe);
-    R kappa = k / me;
-    R eps0 = R(1) / (R(1) + R(2) * kappa);
+    R kappa = mdiv(k, me);
+    R eps0 = mdiv(R(1), R(1) + R(2) * kappa);
     R eps0sq = eps0 * eps0;
     R a1 = -mlog(eps0);
     R a2 = R(0.5) * (R(1) - eps0sq);
     R eps, epssq, onecost, sint2, g;
     for (int trial = 1;; ++trial) {
         R u1 = draw<R>(d), u2 = draw<R>(d), u3 = draw<R>(d);
-        if (a1 / (a1 + a2) > u1) {
+        if (mdiv(a1, a1 + a2) > u1) {
             eps = mexp(-a1 * u2);
             epssq = eps * eps;
         } else {
             epssq = eps0sq + (R(1) - eps0sq) * u2;
             eps = msqrt(epssq);
         }
-        onecost = (R(1) - eps) / (eps * kappa);
+        onecost = mdiv(R(1) - eps, eps * kappa);
         sint2 = onecost * (R(2) - onecost);
-        g = R(1) - eps * sint2 / (R(1) + epssq);
+        g = R(1) - mdiv(eps * sint2, R(1) + epssq);
         if (u3 <= g || trial >= kMaxTrials) break;
     }
     R phi = R(2.0 * kPi) * draw<R>(d);
@@ -1075,9 +1092,9 @@ __device__ __forceinline__ R dipole_one_minus_cos(R T, R u)
     const R me = R(kMe);
     R E = T + me;
     R p = msqrt(T * (T + R(2) * me));
-    R beta = p / E;
-    R a = me * me / (E * (E + p));
-    return R(2) * a * (R(1) - u) / (a + R(2) * beta * u);
+    R beta = mdiv(p, E);
+    R a = mdiv(me * me, E * (E + p));
+    return mdiv(R(2) * a * (R(1) - u), a + R(2) * beta * u);
 }
 
 template <typename R>
@@ -1098,13 +1115,13 @@ __device__ __forceinline__ void emit_dir(const R dir[3], R omc, R phi, R out[3])
 template <typename R>
 __device__ __forceinline__ void sample_rayleigh(Draws& d, R k, R a_screen, R dir[3])
 {
-    R y = k * a_screen / R(kHbarC);
+    R y = mdiv(k * a_screen, R(kHbarC));
     R b = R(2) * y * y;
     R tail = -mexpm1(R(-3) * mlog1p(R(2) * b));
     R x;
     for (int trial = 1;; ++trial) {
         R u1 = draw<R>(d), u2 = draw<R>(d);
-        x = mexpm1(-mlog1p(-u1 * tail) / R(3)) / b;
+        x = mdiv(mexpm1(mdiv(-mlog1p(-u1 * tail), R(3))), b);
         if (x > R(2)) x = R(2);
         if (R(2) * u2 <= R(2) - R(2) * x + x * x || trial >= kMaxTrials) break;
     }
@@ -1129,30 +1146,30 @@ __device__ __forceinline__ R sauter_one_minus_cos(Draws& d, R T)
     const R me = R(kMe);
     R E = T + me;
     R p = msqrt(T * (T + R(2) * me));
-    R beta = p / E;
+    R beta = mdiv(p, E);
     if (!(beta > R(1e-3))) return R(2) * draw<R>(d);
-    R gam = E / me;
-    R a = me * me / (E * (E + p));
+    R gam = mdiv(E, me);
+    R a = mdiv(me * me, E * (E + p));
     R g = R(0.5) * gam * (gam - R(1)) * (gam - R(2));
     R gp = g > R(0) ? g : R(0);
-    R i2a = R(1) / (R(2) * a);
+    R i2a = mdiv(R(1), R(2) * a);
     R w1 = R(0.5) * (i2a * i2a - R(0.25)), w2 = gp * (i2a - R(0.5));
     R v = a;
     for (int trial = 1;; ++trial) {
         R u1 = draw<R>(d), u2 = draw<R>(d), u3 = draw<R>(d);
         if (u1 * (w1 + w2) < w1) {
             R w = i2a * i2a * (R(1) - u2) + R(0.25) * u2;
-            v = R(1) / msqrt(w) - a;
+            v = mdiv(R(1), msqrt(w)) - a;
         } else {
             R w = i2a * (R(1) - u2) + R(0.5) * u2;
-            v = R(1) / w - a;
+            v = mdiv(R(1), w) - a;
         }
         R va = v + a;
-        R f = (v - a) * (R(2) - a - v) * (R(1) + g * v) / (v * v * v * v);
-        R env = R(16) * (R(1) / (va * va * va) + gp / (va * va));
+        R f = mdiv((v - a) * (R(2) - a - v) * (R(1) + g * v), v * v * v * v);
+        R env = R(16) * (mdiv(R(1), va * va * va) + mdiv(gp, va * va));
         if (u3 * env <= f || trial >= kMaxTrials) break;
     }
-    return (v - a) / beta;
+    return mdiv(v - a, beta);
 }
 
 // Highland's width of the projected multiple-scattering angle (PDG review
@@ -1162,11 +1179,11 @@ template <typename R>
 __device__ __forceinline__ R highland(R T, R s, R x0)
 {
     R p = msqrt(T * (T + R(2) * R(kMe)));
-    R beta = p / (T + R(kMe));
-    R t = s / x0;
-    R f = R(1) + R(0.038) * mlog(t / (beta * beta));
+    R beta = mdiv(p, T + R(kMe));
+    R t = mdiv(s, x0);
+    R f = R(1) + R(0.038) * mlog(mdiv(t, beta * beta));
     if (!(f > R(0))) return R(0);
-    return R(13.6) / (beta * p) * msqrt(t) * f;
+    return mdiv(R(13.6), beta * p) * msqrt(t) * f;
 }
 
 // multiple scattering at the end of a step: space angle theta0 sqrt(-2 ln
@@ -1192,7 +1209,7 @@ template <typename R>
 __device__ __forceinline__ void sample_pair(Draws& d, R k, const R dir[3], Products<R>& out, bool angular)
 {
     const R me = R(kMe);
-    R eps0 = me / k;
+    R eps0 = mdiv(me, k);
     R w = R(1) - R(2) * eps0;
     R x;
     for (int trial = 1;; ++trial) {
@@ -1253,12 +1270,12 @@ __device__ __forceinline__ void sample_brems(Draws& d, R T, R kc, const R dir[3]
                                              bool angular)
 {
     R E = T + R(kMe);
-    R lr = mlog(T / kc);
+    R lr = mlog(mdiv(T, kc));
     R k;
     for (int trial = 1;; ++trial) {
         R u1 = draw<R>(d), u2 = draw<R>(d);
         k = kc * mexp(u1 * lr);
-        R y = k / E;
+        R y = mdiv(k, E);
         R f = R(4.0 / 3.0) - R(4.0 / 3.0) * y + y * y;
         if (u2 * R(4.0 / 3.0) <= f || trial >= kMaxTrials) break;
     }
@@ -1285,7 +1302,7 @@ template <typename R>
 __device__ __forceinline__ void delta_kinematics(Draws& d, R T, R Td, R dir[3], Products<R>& out, R& Tnew)
 {
     const R me = R(kMe);
-    R cost = msqrt(Td * (T + R(2) * me) / (T * (Td + R(2) * me)));
+    R cost = msqrt(mdiv(Td * (T + R(2) * me), T * (Td + R(2) * me)));
     if (cost > R(1)) cost = R(1);
     R phi = R(2.0 * kPi) * draw<R>(d);
     R ddir[3];
@@ -1314,16 +1331,16 @@ template <typename R>
 __device__ __forceinline__ void sample_moller(Draws& d, R T, R cut, R dir[3], Products<R>& out, R& Tnew)
 {
     const R me = R(kMe);
-    R xc = cut / T;
-    R g = (T + me) / me;
-    R g1 = (g - R(1)) / g;
-    R c = (R(2) * g - R(1)) / (g * g);
+    R xc = mdiv(cut, T);
+    R g = mdiv(T + me, me);
+    R g1 = mdiv(g - R(1), g);
+    R c = mdiv(R(2) * g - R(1), g * g);
     R gmax = R(2) + R(0.25) * g1 * g1;
     R eps;
     for (int trial = 1;; ++trial) {
         R u1 = draw<R>(d), u2 = draw<R>(d);
-        eps = xc / (R(1) - u1 * (R(1) - R(2) * xc));
-        R q = eps / (R(1) - eps);
+        eps = mdiv(xc, R(1) - u1 * (R(1) - R(2) * xc));
+        R q = mdiv(eps, R(1) - eps);
         R f = R(1) + q * q + g1 * g1 * eps * eps - c * q;
         if (u2 * gmax <= f || trial >= kMaxTrials) break;
     }
@@ -1336,12 +1353,12 @@ template <typename R>
 __device__ __forceinline__ void sample_bhabha(Draws& d, R T, R cut, R dir[3], Products<R>& out, R& Tnew)
 {
     const R me = R(kMe);
-    R xc = cut / T;
-    R g = (T + me) / me;
-    R y = R(1) / (g + R(1));
+    R xc = mdiv(cut, T);
+    R g = mdiv(T + me, me);
+    R y = mdiv(R(1), g + R(1));
     R y2 = y * y;
     R t = R(1) - R(2) * y;
-    R b2 = T * (T + R(2) * me) / ((T + me) * (T + me));
+    R b2 = mdiv(T * (T + R(2) * me), (T + me) * (T + me));
     R c1 = R(2) - y2;
     R c2 = t * (R(3) + y2);
     R c4 = t * t * t;
@@ -1349,7 +1366,7 @@ __device__ __forceinline__ void sample_bhabha(Draws& d, R T, R cut, R dir[3], Pr
     R eps;
     for (int trial = 1;; ++trial) {
         R u1 = draw<R>(d), u2 = draw<R>(d);
-        eps = xc / (R(1) - u1 * (R(1) - xc));
+        eps = mdiv(xc, R(1) - u1 * (R(1) - xc));
         R f = R(1) - b2 * eps * (c1 - eps * (c2 - eps * (c3 - eps * c4)));
         if (u2 <= f || trial >= kMaxTrials) break;
     }
@@ -1363,26 +1380,26 @@ template <typename R>
 __device__ __forceinline__ void sample_annih(Draws& d, R T, const R dir[3], Products<R>& out)
 {
     const R me = R(kMe);
-    R tau = T / me;
+    R tau = mdiv(T, me);
     R g = tau + R(1);
     R a = tau + R(2);
     R s = msqrt(tau * (tau + R(2)));
-    R emin = R(0.5) * (R(1) - s / a);
+    R emin = R(0.5) * (R(1) - mdiv(s, a));
     R emax = R(1) - emin;
-    R lr = mlog(emax / emin);
+    R lr = mlog(mdiv(emax, emin));
     R bq = g * g + R(4) * g + R(1);
     R eps;
     for (int trial = 1;; ++trial) {
         R u1 = draw<R>(d), u2 = draw<R>(d);
         eps = emin * mexp(u1 * lr);
-        R f = R(1) - (a * a * eps + R(1) / eps) / bq;
+        R f = R(1) - mdiv(a * a * eps + mdiv(R(1), eps), bq);
         if (u2 <= f || trial >= kMaxTrials) break;
     }
     R Etot = T + R(2) * me;
     R E1 = eps * Etot;
     R E2 = Etot - E1;
     R pm = msqrt(T * (T + R(2) * me));
-    R cost = Etot * (E1 - me) / (pm * E1);
+    R cost = mdiv(Etot * (E1 - me), pm * E1);
     if (cost > R(1)) cost = R(1);
     if (cost < R(-1)) cost = R(-1);
     R phi = R(2.0 * kPi) * draw<R>(d);

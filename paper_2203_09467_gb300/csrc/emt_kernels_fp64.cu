@@ -1,11 +1,13 @@
-// emt_kernels_fp64.cu -- FP64 instantiation of the step-loop kernels.
-// Built with --fmad=false: every FP64 expression rounds exactly as written,
-// so the path reproduces the FP64 CPU oracle operation by operation.
+// emt_kernels_fp64.cu -- FP64 instantiation of the fused step kernel and
+// the small kernels (the other families: emt_kernels_fp64_{persist,split,
+// pipe}.cu).  Built with --fmad=false: every FP64 expression rounds exactly
+// as written, so the path reproduces the FP64 CPU oracle operation by
+// operation.
 #include "emt_internal.h"
 #include "emt_launch.cuh"
 
 namespace emt {
-template struct Launch<double>;
+EMT_INSTANTIATE_FUSED(double)
 
 // Diagnostics: a barrier that is never reached (it waits for one block
 // more than the launch has), so that every block's bounded wait runs out

@@ -316,3 +316,27 @@ int Launch<R>::max_blocks_pipe(int block)
 }
 
 }  // namespace emt
+
+// Explicit instantiations, split across translation units so that the
+// heavy kernel families compile in parallel.
+#define EMT_INSTANTIATE_FUSED(R)                                                                                    \
+    template cudaError_t Launch<R>::step(const Params<R>&, int, int, int, int, int, int, cudaStream_t);           \
+    template cudaError_t Launch<R>::admit(const Params<R>&, int, int, int, const int32_t*, const int32_t*,         \
+                                          const double*, const double*, const double*, const uint32_t*,         \
+                                          const uint32_t*, cudaStream_t);                                         \
+    template cudaError_t Launch<R>::set_tracks(const Params<R>&, int, int, int, const double*, const uint64_t*,   \
+                                               const int32_t*, cudaStream_t);                                     \
+    template cudaError_t Launch<R>::get_tracks(const Params<R>&, int, int, int, double*, uint64_t*, int32_t*,     \
+                                               cudaStream_t);                                                     \
+    template int Launch<R>::max_blocks_per_sm(int);                                                               \
+    template cudaError_t Launch<R>::unspill(const Params<R>&, int, int, int, cudaStream_t);
+#define EMT_INSTANTIATE_PERSIST(R)                                                                                  \
+    template cudaError_t Launch<R>::persist(const Params<R>&, long long, int, GridSync*, long long, int, int,     \
+                                            cudaStream_t);                                                        \
+    template int Launch<R>::persist_blocks_per_sm(int);
+#define EMT_INSTANTIATE_SPLIT(R)                                                                                    \
+    template cudaError_t Launch<R>::step_split(const Params<R>&, int, int, int, int, int, int, int, cudaStream_t); \
+    template int Launch<R>::max_blocks_split(int, int);
+#define EMT_INSTANTIATE_PIPE(R)                                                                                     \
+    template cudaError_t Launch<R>::step_pipe(const Params<R>&, int, int, int, int, int, int, int, cudaStream_t);  \
+    template int Launch<R>::max_blocks_pipe(int);

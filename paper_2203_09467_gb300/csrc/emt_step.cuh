@@ -199,7 +199,7 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
     int proc = nproc - 1;
     if (gt_zero(sig_tot)) {
         dr.next = 0;
-        s_int = -mlog(draw<R>(dr)) / sig_tot;
+        s_int = mdiv(-mlog(draw<R>(dr)), sig_tot);
         // 9, taken early: the model by draw 1 (the same Philox block as
         // draw 0) against the cumulative pre-step cross sections.  It reads
         // only pre-step values, so it is the choice the step makes if it
@@ -283,8 +283,8 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
         // substeps of at most h_max = sqrt(8 r delta), r = p / (c |B|); at
         // most kMaxSubsteps of them
         const double Td = to_d(t.T);
-        const double pm = sqrt(Td * (Td + 2.0 * kMe));
-        const double hmax = sqrt(8.0 * (pm / (kFieldC * p.bmag)) * p.rk_delta);
+        const double pm = msqrt(Td * (Td + 2.0 * kMe));
+        const double hmax = msqrt(8.0 * mdiv(pm, kFieldC * p.bmag) * p.rk_delta);
         int nsub;
         double hs;
         if (smax > kMaxSubsteps * hmax) {
@@ -292,10 +292,10 @@ __device__ __forceinline__ int transport_part(const Params<R>& p, TrackReg<R>& t
             hs = hmax;
             interact = false;
         } else {
-            double ns = ceil(smax / hmax);
+            double ns = ceil(mdiv(smax, hmax));
             if (ns < 1.0) ns = 1.0;
             nsub = (int)ns;
-            hs = smax / ns;
+            hs = mdiv(smax, ns);
         }
         bool crossed = false;
         s = propagate_field<G>(p, t.type == 1 ? -1 : 1, pm, t.vol, t.x, t.u, nsub, hs, &e, &crossed, &fx.substeps);

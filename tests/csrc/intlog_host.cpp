@@ -1,0 +1,64 @@
+// CPU check of the integer-pipe logarithm (emt_intlog.cuh): prints, for n
+// pseudo-random arguments of each kind, the count that differ from the C
+// library's log, and writes up to `keep` of them (argument, libm, integer
+// path) for a high-precision comparison by the test.
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "../../paper_2203_09467_gb300/csrc/emt_intlog.cuh"
+
+static uint64_t g_s = 88172645463325252ull;
+static uint64_t next()
+{
+    g_s ^= g_s << 13;
+    g_s ^= g_s >> 7;
+    g_s ^= g_s << 17;
+    return g_s;
+}
+static uint64_t bits(double x)
+{
+    uint64_t b;
+    memcpy(&b, &x, 8);
+    return b;
+}
+static double from_bits(uint64_t b)
+{
+    double x;
+    memcpy(&x, &b, 8);
+    return x;
+}
+
+int main(int argc, char** argv)
+{
+    const long n = argc > 1 ? atol(argv[1]) : 1000000;
+    const long keep = argc > 2 ? atol(argv[2]) : 0;
+    const char* path = argc > 3 ? argv[3] : nullptr;
+    FILE* f = path ? fopen(path, "w") : nullptr;
+    long diff = 0, big = 0, kept = 0;
+    for (long i = 0; i < n; ++i) {
+        const uint64_t w = next();
+        double x;
+        switch (i % 4) {
+        case 0: x = (double)(2 * (w >> 12) + 1) * 0x1p-53; break;               // uniforms in (0, 1)
+        case 1: x = 1.0 - (double)((w >> 20) + 1) * 0x1p-53; break;              // just below 1
+        case 2: x = 1.0 + (double)((w >> 20) + 1) * 0x1p-52; break;              // just above 1
+        default: x = from_bits((w >> 2) & 0x7FEFFFFFFFFFFFFFull | 0x0010000000000000ull); break;  // any positive normal
+        }
+        const double a = std::log(x), b = emt::intlog::log_rn(x);
+        if (bits(a) != bits(b)) {
+            ++diff;
+            const long d = (long)(bits(a) - bits(b));
+            if (d > 1 || d < -1) ++big;
+            if (f && kept < keep) {
+                fprintf(f, "%a %a %a\n", x, a, b);
+                ++kept;
+            }
+        }
+    }
+    if (f) fclose(f);
+    printf("%ld %ld %ld\n", n, diff, big);
+    return 0;
+}

@@ -1,0 +1,52 @@
+"""The step kernels' integer-pipe FP64 arithmetic on the GPU: the division
+and square root (emt_intdiv.cuh) bit for bit against the native FP64
+division and square root on 2^31 operand pairs (the FP32 seeds are the
+hardware estimates here), and
+the logarithm (emt_intlog.cuh) within one unit in the last place of the
+native FP64 log, equal to it on all but a small fraction of arguments."""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    out_dir = os.path.join(HERE, "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    so = os.path.join(out_dir, "libintpipe_check.so")
+    subprocess.check_call(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "--fmad=false",
+                           "-std=c++17", "-shared", "-Xcompiler", "-fPIC", "-o", so,
+                           os.path.join(HERE, "csrc", "intpipe_gpu.cu")])
+    L = ctypes.CDLL(so)
+    L.intdiv_check.argtypes = [ctypes.c_ulonglong, ctypes.c_ulonglong, ctypes.c_void_p, ctypes.c_void_p]
+    L.intlog_check.argtypes = [ctypes.c_ulonglong, ctypes.c_ulonglong, ctypes.c_void_p, ctypes.c_void_p]
+    return L
+
+
+def test_integer_division_and_sqrt_equal_native(lib):
+    n = 1 << 31
+    counts = np.zeros(3, np.uint64)
+    ex = np.zeros(16, np.float64)
+    assert lib.intdiv_check(n, 20260, counts.ctypes.data, ex.ctypes.data) == 0
+    assert counts[1] == 0, f"mismatches: {ex.reshape(4, 4)[:int(min(counts[1], 4))]}"
+    assert counts[2] == 0, f"{int(counts[2])} square-root mismatches"
+    assert counts[0] > 0.85 * n
+
+
+def test_integer_log_within_one_ulp_of_native_log(lib):
+    n = 1 << 28
+    counts = np.zeros(4, np.uint64)
+    ex = np.zeros(12, np.float64)
+    assert lib.intlog_check(n, 977, counts.ctypes.data, ex.ctypes.data) == 0
+    assert counts[2] == 0, f"more than one ulp apart: {ex.reshape(4, 3)}"
+    # the integer log is correctly rounded but for ~1e-5 of arguments (CPU
+    # test against a 240-bit reference); the native log is within one ulp
+    assert counts[1] < 2e-3 * n, f"{int(counts[1])} of {n} differ"
+    print(f"integer log differs from the native log on {int(counts[1])} of {n} arguments")
+
