@@ -369,6 +369,8 @@ def gpu_arm(args):
 
     # roofline of the step kernel
     dfma = emt.measure_dfma_rate(local)  # FP64 FMAs per second, measured now on this GPU
+    # FP64 divisions and logarithms per second, native and on the integer pipe
+    op_rates = emt.measure_fp64_op_rates(local)
     peaks, src = load_peaks()
     kern_ms = sum(s["kernel_ms"] for s in stats)
     kern_launch = sum(s["iterations"] for s in stats)  # one step-loop iteration = one step (1 or 2 kernels)
@@ -476,6 +478,7 @@ def gpu_arm(args):
         "gpu_launches": launches,
         "gather": gather,
         "roofline": roof,
+        "fp64_op_rates": op_rates,
         "clocks": clk,
     }
     if roof_hbm:

@@ -383,6 +383,19 @@ emt_status emt_serve(emt_ctx* ctx, int32_t n_events, const uint64_t* event_ids, 
  * the device cannot run it. */
 emt_status emt_measure_dfma_rate(int32_t device, int32_t iters, int32_t repeats, double* fma_per_s);
 
+/* Measurement support (the paper has no counterpart): throughput of FP64
+ * division and natural logarithm on device `device`, native and as the step
+ * kernels compute them on the integer pipe (bit-identical division;
+ * logarithm correctly rounded but for rare arguments), each with
+ * independent chains per thread over eight blocks of 256 threads per SM,
+ * best of `repeats` launches of `iters` iterations (CUDA events); every
+ * operation carries one FP64 addition.  host rates[4] receives operations
+ * per second: native division, integer-pipe division, native log,
+ * integer-pipe log.  Allocates and frees a small buffer of its own.
+ * EMT_ERR_INVALID_ARG for non-positive counts or a null pointer,
+ * EMT_ERR_CUDA if the device cannot run it. */
+emt_status emt_measure_fp64_op_rates(int32_t device, int32_t iters, int32_t repeats, double* rates);
+
 /* Diagnostics of the bounded device wait of EMT_LOOP_PERSISTENT (the
  * paper has no counterpart): launches the same grid barrier on a device
  * with one participant missing, so that its wait can only run out after

@@ -127,6 +127,8 @@ _SIGS = {
     "emt_debug_wait_timeout": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32]),
     "emt_measure_dfma_rate": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                ctypes.POINTER(ctypes.c_double)]),
+    "emt_measure_fp64_op_rates": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                   ctypes.POINTER(ctypes.c_double)]),
     "emt_transport_static": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_uint32, ctypes.POINTER(Material),
                                               ctypes.c_int32, ctypes.POINTER(Physics), ctypes.POINTER(Layer),
                                               ctypes.c_int32, ctypes.POINTER(World), ctypes.c_int32,
@@ -434,3 +436,13 @@ def context_for(setup, **kw) -> Context:
     ctx = Context(**kw)
     ctx.load(setup)
     return ctx
+
+
+def measure_fp64_op_rates(device: int = 0, iters: int = 256, repeats: int = 3) -> dict:
+    """FP64 divisions and logarithms per second of the device, native and on
+    the integer pipe (emt_measure_fp64_op_rates)."""
+    out = (ctypes.c_double * 4)()
+    rc = lib().emt_measure_fp64_op_rates(int(device), int(iters), int(repeats), out)
+    if rc != 0:
+        raise EmtError(rc, "emt_measure_fp64_op_rates failed")
+    return {"div_native": out[0], "div_integer": out[1], "log_native": out[2], "log_integer": out[3]}

@@ -12,7 +12,7 @@ HEADER = os.path.join(ROOT, "include", "emt.h")
 def declared():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(emt_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(emt_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_declares_the_boundary():

@@ -50,3 +50,12 @@ def test_integer_log_within_one_ulp_of_native_log(lib):
     assert counts[1] < 2e-3 * n, f"{int(counts[1])} of {n} differ"
     print(f"integer log differs from the native log on {int(counts[1])} of {n} arguments")
 
+
+def test_op_rate_probe_through_the_abi():
+    """emt_measure_fp64_op_rates (the benchmark reports it): all four rates
+    are measured; on GB300 the integer-pipe forms are the faster ones."""
+    from paper_2203_09467_gb300 import emt
+    r = emt.measure_fp64_op_rates(0, iters=64, repeats=1)
+    assert set(r) == {"div_native", "div_integer", "log_native", "log_integer"}
+    assert all(v > 0 for v in r.values())
+    print({k: f"{v:.3e}" for k, v in r.items()})
