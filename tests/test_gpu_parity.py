@@ -53,9 +53,14 @@ def compare_events(summ, osumm, hist=None, ohist=None, frac=0.999):
     assert same.mean() >= frac, f"identical step/track counts on {same.mean():.4f} of events"
     led = np.abs(summ[:, 3] - summ[:, 0] - summ[:, 1] - summ[:, 2]) / summ[:, 3]
     assert led.max() <= TOL, f"energy ledger {led.max():.3e}"
+    worst_bin = None
     if hist is not None:
         hrel = np.abs(hist - ohist).max(axis=1) / e_in
         assert (hrel <= TOL).mean() >= frac
+        worst_bin = float(hrel.max())
+    # the measured agreement (shown with pytest -s or -rA)
+    print(f"parity on {len(rel)} events: totals within {TOL:g} E_in on {ok.mean():.4f}, worst {rel.max():.2e} E_in; "
+          f"identical counts on {same.mean():.4f}; worst bin {worst_bin if worst_bin is None else f'{worst_bin:.2e}'} E_in")
     return rel
 
 
