@@ -82,6 +82,27 @@ int main(int argc, char** argv)
             ++sbad;
         }
     }
-    printf("%ld %ld %ld\n", n, fast, bad + sbad);
-    return bad + sbad != 0;
+    // special operands: zeros, subnormals, infinities, NaNs, the ends of the
+    // normal range and quotients that overflow or underflow
+    const double sp[] = {0.0, -0.0, 0x1p-1074, -0x1p-1074, 0x1p-1022, 0x1.fffffffffffffp-1023, 0x1.fffffffffffffp+1023,
+                         -0x1.fffffffffffffp+1023, 1.0, -1.0, 3.0, 0x1p+1000, 0x1p-1000, 1.0 / 0.0, -1.0 / 0.0,
+                         0.0 / 0.0, 0x1.8p-1070, 2.5e-310, 7.0};
+    long xbad = 0;
+    for (double x : sp)
+        for (double y : sp) {
+            const double q0 = x / y, q1 = emt::intdiv::div_rn(x, y);
+            if (dbits(q0) != dbits(q1) && !(q0 != q0 && q1 != q1)) {
+                printf("special mismatch %a / %a: %a, integer path %a\n", x, y, q0, q1);
+                ++xbad;
+            }
+        }
+    for (double x : sp) {
+        const double r0 = std::sqrt(x), r1 = emt::intdiv::sqrt_rn(x);
+        if (dbits(r0) != dbits(r1) && !(r0 != r0 && r1 != r1)) {
+            printf("special sqrt mismatch %a: %a, integer path %a\n", x, r0, r1);
+            ++xbad;
+        }
+    }
+    printf("%ld %ld %ld\n", n, fast, bad + sbad + xbad);
+    return bad + sbad + xbad != 0;
 }

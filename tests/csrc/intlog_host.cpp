@@ -59,6 +59,17 @@ int main(int argc, char** argv)
         }
     }
     if (f) fclose(f);
+    // special arguments take the native log (or agree with it exactly)
+    const double sp[] = {0.0, -0.0, 0x1p-1074, 0x1p-1022, 0x1.fffffffffffffp+1023, 1.0, -1.0, 1.0 / 0.0, -1.0 / 0.0,
+                         0.0 / 0.0, 0.75, 1.5, 0x1.7ffffffffffffp+0, 0x1.8p-1, 0x1.fep-1, 0x1.01p+0, 2.0, 0.5};
+    for (double x : sp) {
+        const double a = std::log(x), b = emt::intlog::log_rn(x);
+        if (bits(a) != bits(b) && !(a != a && b != b)) {
+            const long d = (long)(bits(a) - bits(b));
+            ++diff;
+            if (d > 1 || d < -1 || (a != a) != (b != b)) ++big;
+        }
+    }
     printf("%ld %ld %ld\n", n, diff, big);
     return 0;
 }
