@@ -26,8 +26,6 @@
 //      R move A R / 2^62 by less than 2^-7).
 //   3. The exact remainder A 2^53 - Q B (|.| < 2^54, so its low 64 bits
 //      are the whole value) corrects Q by one where needed.
-// The FP32 reciprocal is the only floating-point step; its exact value does
-// not matter, only its error bound.
 //
 // `sqrt_rn(x)` does the same for the square root: with x = N 2^(2k - 52),
 // N in [2^52, 2^54), the result significand is RN(sqrt(N 2^52)), never a
@@ -35,9 +33,13 @@
 // Q' = floor(sqrt(N 2^54)) suffices; Y ~ 2^63 / sqrt(N 2^-52) from an FP32
 // reciprocal square root and two Newton steps Y += Y (1 - N Y^2 2^-178) / 2,
 // Q = floor(N Y / 2^62) within one of Q', corrected by the exact remainder
-// N 2^54 - Q^2 (|.| < 2^56).  Host builds (the CPU test of this file)
-// use a correctly rounded FP32 quotient in its place, moved by up to three
-// units of its last place to cover the hardware estimate's error.
+// N 2^54 - Q^2 (|.| < 2^56).
+//
+// The FP32 reciprocal (square root) estimates are the only floating-point
+// steps; their exact values do not matter, only their error bounds.  Host
+// builds (the CPU test of this file) use correctly rounded FP32 results in
+// their place, moved by up to three units of the last place to cover the
+// hardware estimates' errors.
 #pragma once
 
 #include <stdint.h>
