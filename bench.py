@@ -49,7 +49,7 @@ METRIC = "track-steps/s"
 # precision and step schedule.  Reported only while the kernel sources are
 # the ones that were measured (SHA-256 below).
 TRAFFIC = {
-    "kernel_sha256": "9833f68138a586bfd380b9a74961298fb128ca4371062c801605e99c0767aa68",
+    "kernel_sha256": "15abf5842738ce5d4e9c433fb3bef2edc32a6368716462450f708d34bdded67d",
     "bytes_per_track_step": {"calo/fp64/pipelined": 101.6, "calo/fp64/split": 114.4, "calo/mixed/pipelined": 97.5,
                              "calo_field/fp64/split": 109.1},
     "source": "profiles/step_kernels_dram_traffic.md",

@@ -15,10 +15,12 @@
 // multiple of 2^-116 (2^-128 next to x = 1, where the result is ln(1 + r)
 // alone and may be tiny) and is rounded once to the nearest double.  The
 // result is the correctly rounded logarithm except when ln x lies within
-// about 2^-75 (relative) of a rounding boundary.  On 4e6 arguments (uniforms,
-// both sides of 1, any positive normal) it differs from the C library's log
-// in 2.1e-4 of them, by one unit in the last place, and a 240-bit reference
-// sides with it in every one of those cases.  Non-positive, subnormal and
+// about 2^-75 (relative) of a rounding boundary.  On 4e6 random arguments
+// (uniforms, both sides of 1, any positive normal) it differs from the C
+// library's log in 2.1e-4 of them, by one unit in the last place, and a
+// 240-bit reference sides with it in every one of those cases.  Arguments
+// x = 1 - k 2^-53 with small k are such exceptions: their logarithm lies
+// within 1e-11 units of a midpoint, finer than the fixed-point sum.  Non-positive, subnormal and
 // non-finite arguments take the native log.
 #pragma once
 

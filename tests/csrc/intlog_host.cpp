@@ -59,6 +59,32 @@ int main(int argc, char** argv)
         }
     }
     if (f) fclose(f);
+    // the edges of every reduction interval (X = 0.75 + j 2^-8 and one unit
+    // either side), of the [0.75, 1.5) normalisation, and 1 +- k units
+    for (int j = 0; j <= 192; ++j) {
+        const double X = 0.75 + j * 0x1p-8;
+        for (int e = -3; e <= 3; e += 3) {
+            const double c = std::ldexp(X, e);
+            for (int k = -2; k <= 2; ++k) {
+                const double x = from_bits(bits(c) + (uint64_t)(int64_t)k);
+                const double a = std::log(x), b = emt::intlog::log_rn(x);
+                if (bits(a) != bits(b)) {
+                    ++diff;
+                    const long d = (long)(bits(a) - bits(b));
+                    if (d > 1 || d < -1) ++big;
+                }
+            }
+        }
+    }
+    for (int k = -2000; k <= 2000; ++k) {
+        const double x = from_bits(bits(1.0) + (uint64_t)(int64_t)k);
+        const double a = std::log(x), b = emt::intlog::log_rn(x);
+        if (bits(a) != bits(b)) {
+            ++diff;
+            const long d = (long)(bits(a) - bits(b));
+            if (d > 1 || d < -1) ++big;
+        }
+    }
     // special arguments take the native log (or agree with it exactly)
     const double sp[] = {0.0, -0.0, 0x1p-1074, 0x1p-1022, 0x1.fffffffffffffp+1023, 1.0, -1.0, 1.0 / 0.0, -1.0 / 0.0,
                          0.0 / 0.0, 0.75, 1.5, 0x1.7ffffffffffffp+0, 0x1.8p-1, 0x1.fep-1, 0x1.01p+0, 2.0, 0.5};
